@@ -1,0 +1,427 @@
+/*
+ * FP64 CPU oracle for incompressible-flow P1 tetrahedral matrix assembly.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA library is checked against.  Only the test suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may load it; the library never does.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * What is computed (Section II-A, Listings 1 and 2 of the paper; the per-term
+ * formulas are the Galerkin P1 form, since the paper names the subroutines
+ * but not their equations):
+ *
+ *   per linear tetrahedron e with nodes lnods[e][0..3] (4 nodes, 3 dims):
+ *     gather      elcod[a][i] = coord[lnods[e][a]][i], elvel likewise
+ *                 (calculate_transients, Listing 2)
+ *     Jacobian    J[i][j] = d x_i / d xi_j = sum_a elcod[a][i] dN_a/dxi_j
+ *                 det J, J^{-1} by cofactors, gpcar[a][i] = dN_a/dx_i
+ *                 = sum_j Jinv[j][i] dN_a/dxi_j, gpvol[g] = w_g det J
+ *                 (calculate_cartesian_derivatives, Listing 1)
+ *     Gauss pts   4-point rule, barycentric (alpha, beta, beta, beta) and its
+ *                 permutations, reference weight 1/24 each; beta=(5-sqrt 5)/20,
+ *                 alpha = 1 - 3 beta (the printed 10-digit constants rounded)
+ *     gp values   gpvel[g][k] = sum_c N_c(xi_g) elvel[c][k]
+ *                 (calculate_gauss_point_values)
+ *     matrices    agrau[g][b] = gpvel[g] . gpcar[b]; wgrgr[a][b] = gpcar[a].gpcar[b]
+ *                 (calculate_element_matricies)
+ *     A_e[a][b]   = sum_g gpvol[g] ( rho N_a(xi_g) agrau[g][b] + mu wgrgr[a][b] )
+ *                   + delta_ab rho/dt sum_g gpvol[g] N_a(xi_g)   (row-sum lumped mass)
+ *                 (calculate_convective_term_and_RHS, calculate_viscous_term)
+ *     G_e[a][b][d]= - sum_g gpvol[g] gpcar[a][d] N_b(xi_g)
+ *     b_e[a][k]   = rho/dt (sum_g gpvol[g] N_a(xi_g)) un[a][k]   (lumped RHS)
+ *   assembly      A[row lnods[a], col lnods[b]] += A_e[a][b], G likewise on
+ *                 the same CSR pattern, rhs[k][lnods[a]] += b_e[a][k]
+ *                 (perform_assembly_in_global_system, Listing 2; here into a
+ *                 CSR matrix), contributions added in increasing element order.
+ *
+ * Layouts: coord/u/un/w are node-major [n][3] (the paper's coord(3,npoin) with
+ * the dimension fastest); lnods is [E][4], 0-based; CSR row_ptr[n+1],
+ * col_idx[nnz] ascending per row, diagonal included; G is component-major
+ * [3][nnz]; rhs is [3][n].
+ *
+ * All arithmetic is IEEE double (the paper: all calculations are double
+ * precision, Section II-A).  Return codes: 0 ok, negative on bad input.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PNODE 4
+#define PGAUS 4
+#define NDIME 3
+
+/* reference-element shape derivatives dN_a/dxi_j: N_0 = 1-xi-eta-zeta, N_j = xi_j */
+static const double DERIV[PNODE][NDIME] = {
+    {-1.0, -1.0, -1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+
+/* shape function values N_c(xi_g) at the 4 Gauss points (barycentric coordinates) */
+static void gauss_rule(double shape[PGAUS][PNODE], double weight[PGAUS]) {
+    const double beta = (5.0 - sqrt(5.0)) / 20.0;
+    const double alpha = 1.0 - 3.0 * beta;
+    for (int g = 0; g < PGAUS; ++g) {
+        for (int c = 0; c < PNODE; ++c) shape[g][c] = (c == g) ? alpha : beta;
+        weight[g] = 1.0 / 24.0; /* reference tet volume 1/6 split over 4 points */
+    }
+}
+
+/*
+ * Jacobian J[i][j] = dx_i/dxi_j, its determinant and inverse (by cofactors),
+ * and the Cartesian shape derivatives gpcar[a][i] = dN_a/dx_i = sum_j
+ * Jinv[j][i] dN_a/dxi_j (calculate_cartesian_derivatives, Listing 1).
+ * Returns det J.
+ */
+static double cartesian_derivatives(const double X[PNODE][NDIME], double gpcar[PNODE][NDIME]) {
+    double J[NDIME][NDIME];
+    for (int i = 0; i < NDIME; ++i)
+        for (int j = 0; j < NDIME; ++j) {
+            J[i][j] = 0.0;
+            for (int a = 0; a < PNODE; ++a) J[i][j] += X[a][i] * DERIV[a][j];
+        }
+    /* cofactor matrix C[i][j] = (-1)^{i+j} minor(i, j) */
+    double C[NDIME][NDIME];
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = -(J[1][0] * J[2][2] - J[1][2] * J[2][0]);
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = -(J[0][1] * J[2][2] - J[0][2] * J[2][1]);
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = -(J[0][0] * J[2][1] - J[0][1] * J[2][0]);
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = -(J[0][0] * J[1][2] - J[0][2] * J[1][0]);
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    /* J^{-1} = adj(J) / det with adj(J)[j][i] = C[i][j] */
+    double Jinv[NDIME][NDIME];
+    for (int i = 0; i < NDIME; ++i)
+        for (int j = 0; j < NDIME; ++j) Jinv[i][j] = C[j][i] / det;
+    for (int a = 0; a < PNODE; ++a)
+        for (int i = 0; i < NDIME; ++i) {
+            gpcar[a][i] = 0.0;
+            for (int j = 0; j < NDIME; ++j) gpcar[a][i] += Jinv[j][i] * DERIV[a][j];
+        }
+    return det;
+}
+
+/*
+ * Element matrices for one tetrahedron (Listing 1 subroutines, in order).
+ * X: node coordinates, U: advection velocity, Un: velocity used by the RHS.
+ * Returns det J (negative or zero for an inverted/degenerate element).
+ */
+double oracle_element(const double X[PNODE][NDIME], const double U[PNODE][NDIME],
+                      const double Un[PNODE][NDIME], double rho, double mu, double dt,
+                      double A[PNODE][PNODE], double G[PNODE][PNODE][NDIME],
+                      double b[PNODE][NDIME], double* volume) {
+    double shape[PGAUS][PNODE], weight[PGAUS];
+    gauss_rule(shape, weight);
+
+    double gpcar[PGAUS][PNODE][NDIME], gpvol[PGAUS], detjac = 0.0;
+    /* calculate_cartesian_derivatives: loop over Gauss points (constant for P1) */
+    for (int g = 0; g < PGAUS; ++g) {
+        detjac = cartesian_derivatives(X, gpcar[g]);
+        gpvol[g] = weight[g] * detjac;
+    }
+
+    /* calculate_gauss_point_values: advection velocity at each Gauss point */
+    double gpvel[PGAUS][NDIME];
+    for (int g = 0; g < PGAUS; ++g)
+        for (int k = 0; k < NDIME; ++k) {
+            gpvel[g][k] = 0.0;
+            for (int c = 0; c < PNODE; ++c) gpvel[g][k] += shape[g][c] * U[c][k];
+        }
+
+    memset(A, 0, sizeof(double) * PNODE * PNODE);
+    memset(G, 0, sizeof(double) * PNODE * PNODE * NDIME);
+    memset(b, 0, sizeof(double) * PNODE * NDIME);
+    double vol = 0.0;
+    for (int g = 0; g < PGAUS; ++g) {
+        /* calculate_element_matricies */
+        double agrau[PNODE], wgrgr[PNODE][PNODE];
+        for (int bb = 0; bb < PNODE; ++bb) {
+            agrau[bb] = 0.0;
+            for (int k = 0; k < NDIME; ++k) agrau[bb] += gpvel[g][k] * gpcar[g][bb][k];
+        }
+        for (int a = 0; a < PNODE; ++a)
+            for (int bb = 0; bb < PNODE; ++bb) {
+                wgrgr[a][bb] = 0.0;
+                for (int k = 0; k < NDIME; ++k) wgrgr[a][bb] += gpcar[g][a][k] * gpcar[g][bb][k];
+            }
+        /* convective + viscous terms */
+        for (int a = 0; a < PNODE; ++a)
+            for (int bb = 0; bb < PNODE; ++bb)
+                A[a][bb] += gpvol[g] * (rho * shape[g][a] * agrau[bb] + mu * wgrgr[a][bb]);
+        /* pressure-gradient block */
+        for (int a = 0; a < PNODE; ++a)
+            for (int bb = 0; bb < PNODE; ++bb)
+                for (int d = 0; d < NDIME; ++d) G[a][bb][d] -= gpvol[g] * gpcar[g][a][d] * shape[g][bb];
+        vol += gpvol[g];
+    }
+    /* row-sum lumped mass on the diagonal and lumped RHS */
+    for (int a = 0; a < PNODE; ++a) {
+        double lump = 0.0;
+        for (int g = 0; g < PGAUS; ++g) lump += gpvol[g] * shape[g][a];
+        A[a][a] += rho * lump / dt;
+        for (int k = 0; k < NDIME; ++k) b[a][k] = rho * lump * Un[a][k] / dt;
+    }
+    if (volume) *volume = vol;
+    return detjac;
+}
+
+static void gather(const double* coord, const double* u, const double* un, const int32_t* ln,
+                   double X[PNODE][NDIME], double U[PNODE][NDIME], double Un[PNODE][NDIME]) {
+    /* calculate_transients (Listing 2) */
+    for (int a = 0; a < PNODE; ++a) {
+        int64_t p = ln[a];
+        for (int k = 0; k < NDIME; ++k) {
+            X[a][k] = coord[3 * p + k];
+            U[a][k] = u[3 * p + k];
+            Un[a][k] = un[3 * p + k];
+        }
+    }
+}
+
+/* element matrices for a list of elements: A[m][4][4], G[m][4][4][3], b[m][4][3], vol[m], det[m] */
+int oracle_element_batch(int64_t n, const double* coord, const int32_t* lnods, const double* u,
+                         const double* un, double rho, double mu, double dt, const int64_t* elems,
+                         int64_t m, double* A, double* G, double* b, double* vol, double* det) {
+    for (int64_t t = 0; t < m; ++t) {
+        const int32_t* ln = lnods + 4 * elems[t];
+        for (int a = 0; a < PNODE; ++a)
+            if (ln[a] < 0 || ln[a] >= n) return -1;
+        double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
+        gather(coord, u, un, ln, X, U, Un);
+        det[t] = oracle_element(X, U, Un, rho, mu, dt, (double(*)[PNODE])(A + 16 * t),
+                                (double(*)[PNODE][NDIME])(G + 48 * t), (double(*)[NDIME])(b + 12 * t),
+                                vol + t);
+    }
+    return 0;
+}
+
+static int cmp_i64(const void* x, const void* y) {
+    int64_t a = *(const int64_t*)x, c = *(const int64_t*)y;
+    return (a > c) - (a < c);
+}
+
+/*
+ * CSR pattern of the assembled matrix: every pair (lnods[e][a], lnods[e][b]),
+ * sorted by (row, col), duplicates removed.  Call with col_idx == NULL to get
+ * nnz only; then call again with col_idx sized nnz.  Returns nnz or < 0.
+ */
+int64_t oracle_pattern(int64_t n, int64_t E, const int32_t* lnods, int32_t* row_ptr, int32_t* col_idx) {
+    int64_t npairs = 16 * E;
+    int64_t* key = (int64_t*)malloc(sizeof(int64_t) * (npairs > 0 ? npairs : 1));
+    if (!key) return -2;
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 4; ++c) {
+                int64_t r = lnods[4 * e + a], s = lnods[4 * e + c];
+                if (r < 0 || r >= n || s < 0 || s >= n) { free(key); return -1; }
+                key[16 * e + 4 * a + c] = r * n + s;
+            }
+    qsort(key, npairs, sizeof(int64_t), cmp_i64);
+    int64_t nnz = 0;
+    for (int64_t t = 0; t < npairs; ++t)
+        if (t == 0 || key[t] != key[t - 1]) {
+            if (col_idx) col_idx[nnz] = (int32_t)(key[t] % n);
+            ++nnz;
+        }
+    if (col_idx && row_ptr) {
+        for (int64_t i = 0; i <= n; ++i) row_ptr[i] = 0;
+        int64_t q = 0;
+        for (int64_t t = 0; t < npairs; ++t)
+            if (t == 0 || key[t] != key[t - 1]) {
+                row_ptr[key[t] / n + 1] += 1;
+                ++q;
+            }
+        for (int64_t i = 0; i < n; ++i) row_ptr[i + 1] += row_ptr[i];
+    }
+    free(key);
+    return nnz;
+}
+
+static int64_t find_pos(const int32_t* row_ptr, const int32_t* col_idx, int64_t r, int64_t c) {
+    int64_t lo = row_ptr[r], hi = row_ptr[r + 1] - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (col_idx[mid] == c) return mid;
+        if (col_idx[mid] < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Global assembly into the oracle's CSR pattern (outputs zeroed here). */
+int oracle_assemble(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
+                    const double* un, double rho, double mu, double dt, const int32_t* row_ptr,
+                    const int32_t* col_idx, double* A, double* G, double* rhs) {
+    int64_t nnz = row_ptr[n];
+    memset(A, 0, sizeof(double) * nnz);
+    memset(G, 0, sizeof(double) * 3 * nnz);
+    memset(rhs, 0, sizeof(double) * 3 * n);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        for (int a = 0; a < PNODE; ++a)
+            if (ln[a] < 0 || ln[a] >= n) return -1;
+        double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
+        double Ae[PNODE][PNODE], Ge[PNODE][PNODE][NDIME], be[PNODE][NDIME], vol;
+        gather(coord, u, un, ln, X, U, Un);
+        oracle_element(X, U, Un, rho, mu, dt, Ae, Ge, be, &vol);
+        /* perform_assembly_in_global_system */
+        for (int a = 0; a < PNODE; ++a) {
+            for (int c = 0; c < PNODE; ++c) {
+                int64_t pos = find_pos(row_ptr, col_idx, ln[a], ln[c]);
+                if (pos < 0) return -3;
+                A[pos] += Ae[a][c];
+                for (int d = 0; d < NDIME; ++d) G[d * nnz + pos] += Ge[a][c][d];
+            }
+            for (int k = 0; k < NDIME; ++k) rhs[k * n + ln[a]] += be[a][k];
+        }
+    }
+    return 0;
+}
+
+/*
+ * The same assembly restricted to a list of rows (for spot checks on meshes too
+ * large for the full oracle).  For sampled row t (t < m), the row's columns
+ * (ascending) go to cols[t*maxc ...], count[t] holds their number, A/G/rhs
+ * hold the values: A[t*maxc + q], G[(t*3 + d)*maxc + q], rhs[t*3 + k].
+ * Contributions are added in increasing element order.
+ */
+int oracle_assemble_rows(int64_t n, int64_t E, const double* coord, const int32_t* lnods,
+                         const double* u, const double* un, double rho, double mu, double dt,
+                         const int64_t* rows, int64_t m, int64_t maxc, int32_t* cols, int32_t* count,
+                         double* A, double* G, double* rhs) {
+    int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    if (!slot) return -2;
+    for (int64_t i = 0; i < n; ++i) slot[i] = -1;
+    for (int64_t t = 0; t < m; ++t) {
+        if (rows[t] < 0 || rows[t] >= n || slot[rows[t]] >= 0) { free(slot); return -1; }
+        slot[rows[t]] = t;
+        count[t] = 0;
+    }
+    memset(A, 0, sizeof(double) * m * maxc);
+    memset(G, 0, sizeof(double) * m * 3 * maxc);
+    memset(rhs, 0, sizeof(double) * m * 3);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        int hit = 0;
+        for (int a = 0; a < PNODE; ++a) {
+            if (ln[a] < 0 || ln[a] >= n) { free(slot); return -1; }
+            hit |= slot[ln[a]] >= 0;
+        }
+        if (!hit) continue;
+        double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
+        double Ae[PNODE][PNODE], Ge[PNODE][PNODE][NDIME], be[PNODE][NDIME], vol;
+        gather(coord, u, un, ln, X, U, Un);
+        oracle_element(X, U, Un, rho, mu, dt, Ae, Ge, be, &vol);
+        for (int a = 0; a < PNODE; ++a) {
+            int64_t t = slot[ln[a]];
+            if (t < 0) continue;
+            for (int c = 0; c < PNODE; ++c) {
+                int64_t q = 0;
+                while (q < count[t] && cols[t * maxc + q] != ln[c]) ++q;
+                if (q == count[t]) {
+                    if (q >= maxc) { free(slot); return -4; }
+                    cols[t * maxc + q] = ln[c];
+                    count[t] += 1;
+                }
+                A[t * maxc + q] += Ae[a][c];
+                for (int d = 0; d < NDIME; ++d) G[(t * 3 + d) * maxc + q] += Ge[a][c][d];
+            }
+            for (int k = 0; k < NDIME; ++k) rhs[t * 3 + k] += be[a][k];
+        }
+    }
+    /* sort each row by column (insertion sort; values move with their column) */
+    for (int64_t t = 0; t < m; ++t) {
+        for (int32_t q = 1; q < count[t]; ++q) {
+            for (int32_t r = q; r > 0 && cols[t * maxc + r - 1] > cols[t * maxc + r]; --r) {
+                int64_t i0 = t * maxc + r - 1, i1 = t * maxc + r;
+                int32_t tc = cols[i0]; cols[i0] = cols[i1]; cols[i1] = tc;
+                double ta = A[i0]; A[i0] = A[i1]; A[i1] = ta;
+                for (int d = 0; d < NDIME; ++d) {
+                    int64_t j0 = (t * 3 + d) * maxc + r - 1, j1 = j0 + 1;
+                    double tg = G[j0]; G[j0] = G[j1]; G[j1] = tg;
+                }
+            }
+        }
+    }
+    free(slot);
+    return 0;
+}
+
+/*
+ * Adjoint of the assembled residual R = A(u) u - b (b held fixed):
+ *   grad_u[m][l] = sum_{i,k} w[i][k] dR[i][k]/du[m][l]
+ *   grad_mu      = sum_{i,k} w[i][k] dR[i][k]/dmu
+ * Per element, from the Gauss-point form of R_e[a][k] =
+ *   sum_g gpvol_g ( rho N_a(g) gpvel_g . grad u^k + mu gpcar_a . grad u^k )
+ *   + rho/dt lump_a u[a][k] - b_e[a][k],     grad u^k = sum_c u[c][k] gpcar_c,
+ * differentiated term by term:
+ *   dR_e[a][k]/du[m][l] = sum_g gpvol_g ( rho N_a(g) N_m(g) (grad u^k)_l
+ *                          + delta_kl (rho N_a(g) gpvel_g . gpcar_m + mu gpcar_a . gpcar_m) )
+ *                          + delta_kl delta_am rho/dt lump_a
+ *   dR_e[a][k]/dmu      = sum_g gpvol_g gpcar_a . grad u^k
+ * w, u, grad_u are node-major [n][3].  grad_u is overwritten.
+ */
+int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
+               double rho, double mu, double dt, const double* w, double* grad_u, double* grad_mu) {
+    double shape[PGAUS][PNODE], weight[PGAUS];
+    gauss_rule(shape, weight);
+    memset(grad_u, 0, sizeof(double) * 3 * n);
+    double gmu = 0.0;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        for (int a = 0; a < PNODE; ++a)
+            if (ln[a] < 0 || ln[a] >= n) return -1;
+        double X[PNODE][NDIME], U[PNODE][NDIME], W[PNODE][NDIME];
+        for (int a = 0; a < PNODE; ++a)
+            for (int k = 0; k < NDIME; ++k) {
+                X[a][k] = coord[3 * (int64_t)ln[a] + k];
+                U[a][k] = u[3 * (int64_t)ln[a] + k];
+                W[a][k] = w[3 * (int64_t)ln[a] + k];
+            }
+        double gpcar[PNODE][NDIME], gpvol[PGAUS];
+        double det = cartesian_derivatives(X, gpcar);
+        for (int g = 0; g < PGAUS; ++g) gpvol[g] = weight[g] * det;
+        /* velocity gradient grad u^k (constant on a P1 element) */
+        double gradu[NDIME][NDIME]; /* gradu[k][l] = d u^k / d x_l */
+        for (int k = 0; k < NDIME; ++k)
+            for (int l = 0; l < NDIME; ++l) {
+                gradu[k][l] = 0.0;
+                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * gpcar[c][l];
+            }
+        for (int g = 0; g < PGAUS; ++g) {
+            double gpvel[NDIME];
+            for (int k = 0; k < NDIME; ++k) {
+                gpvel[k] = 0.0;
+                for (int c = 0; c < PNODE; ++c) gpvel[k] += shape[g][c] * U[c][k];
+            }
+            for (int a = 0; a < PNODE; ++a)
+                for (int mm = 0; mm < PNODE; ++mm) {
+                    double adv_m = 0.0, visc_am = 0.0;
+                    for (int i = 0; i < NDIME; ++i) {
+                        adv_m += gpvel[i] * gpcar[mm][i];
+                        visc_am += gpcar[a][i] * gpcar[mm][i];
+                    }
+                    for (int k = 0; k < NDIME; ++k)
+                        for (int l = 0; l < NDIME; ++l) {
+                            double d = rho * shape[g][a] * shape[g][mm] * gradu[k][l];
+                            if (k == l) d += rho * shape[g][a] * adv_m + mu * visc_am;
+                            grad_u[3 * (int64_t)ln[mm] + l] += W[a][k] * gpvol[g] * d;
+                        }
+                }
+            for (int a = 0; a < PNODE; ++a)
+                for (int k = 0; k < NDIME; ++k) {
+                    double dmu = 0.0;
+                    for (int i = 0; i < NDIME; ++i) dmu += gpcar[a][i] * gradu[k][i];
+                    gmu += W[a][k] * gpvol[g] * dmu;
+                }
+        }
+        /* lumped mass term */
+        for (int a = 0; a < PNODE; ++a) {
+            double lump = 0.0;
+            for (int g = 0; g < PGAUS; ++g) lump += gpvol[g] * shape[g][a];
+            for (int k = 0; k < NDIME; ++k) grad_u[3 * (int64_t)ln[a] + k] += W[a][k] * rho * lump / dt;
+        }
+    }
+    *grad_mu = gmu;
+    return 0;
+}
