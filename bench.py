@@ -1,0 +1,409 @@
+"""Benchmark: tetrahedral elements assembled per second on GB300.
+
+Workload (default): the 100^3-hex unit cube split into 6,000,000 Kuhn tets
+(1,030,301 nodes, nnz 15,210,901), interior nodes jittered by +-15% h, node
+numbering a seeded random permutation; rho = 1, mu = 1e-3, dt = 1e-2;
+velocity = seeded sum of sinusoids.  One step = one full assembly of A
+(CSR), G (3 CSR value arrays) and rhs through the C ABI, inputs resident in
+HBM, outputs overwritten.  Mixed precision (float gathers and element
+arithmetic, compensated accumulation stored as double) is the headline; the
+plain FP64 mode is timed beside it.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank assembles its own
+replica of the workload (no data-path collective) and value is the total
+over ranks.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import meshgen  # noqa: E402
+
+WORKLOADS = {
+    "cube100": "Kuhn cube 100^3 hexes, 6,000,000 tets, 1,030,301 nodes, jitter 15% h, random numbering, seed 1",
+    "cube8": "Kuhn cube 8^3 hexes, 3,072 tets, 729 nodes, natural numbering, seed 0",
+    "cube200_rcm": "Kuhn cube 200^3 hexes, 48,000,000 tets, 8,120,601 nodes, jitter 15% h, RCM numbering, 5% noise",
+    "cube200_random": "Kuhn cube 200^3 hexes, 48,000,000 tets, 8,120,601 nodes, jitter 15% h, random numbering, 5% noise",
+}
+PREC_BYTES = {"fp64": (8, 8, 8), "mixed64": (8, 4, 8), "mixed32": (8, 4, 4)}  # coord, velocity, output
+
+
+def algorithmic_bytes(E, n, nnz, precision):
+    """Compulsory HBM bytes of one assembly: connectivity 16 B/tet, coordinates,
+    velocities, CSR pattern (row_ptr + col_idx), A + 3 G value arrays, 3 rhs."""
+    sx, su, so = PREC_BYTES[precision]
+    return 16 * E + n * (3 * sx + 3 * su) + 4 * (n + 1) + 4 * nnz + so * 4 * nnz + so * 3 * n
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2111_05651_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel, workload, precision):
+    """ncu DRAM bytes per launch, committed under profiles/, if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+        key = f"{kernel}|{workload}|{precision}"
+        r = rec.get(key)
+        if r and r.get("csrc_hash") == csrc_hash():
+            return r["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, period_ms=20):
+        self.index, self.period, self.lines, self.proc, self.t0, self.t1 = index, period_ms, [], None, None, None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms", str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)  # let the first samples arrive
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        inside = [l for (t, l) in self.lines if self.t0 is not None and self.t0 <= t <= self.t1 + 0.05]
+        note = None
+        if len(inside) < 2:
+            # the timed region is shorter than the sampling period: take the samples next to it
+            near = sorted(self.lines, key=lambda x: abs(x[0] - (self.t0 or x[0])))[:4]
+            inside = [l for _, l in near]
+            note = "timed region shorter than the sampling period; nearest samples used"
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in inside:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+               "samples": len(sm), "power_w_max": max(power) if power else None}
+        if note:
+            out["note"] = note
+        return out
+
+
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- CPU oracle ---
+def cpu_oracle_rate(mesh, u, n_elems, repeats=3):
+    """Elements/s of the FP64 oracle (one host thread) on the first n_elems tets."""
+    import oracle
+
+    ln = mesh.lnods[:n_elems]
+    csr = oracle.pattern(mesh.n_nodes, ln)
+    times = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        times.append(time.perf_counter() - t)
+    return n_elems / statistics.median(times), statistics.median(times)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    mesh, u = meshgen.config_mesh(args.workload)
+    n_s = min(args.ref_sample, mesh.n_elems)
+    ln = mesh.lnods[:n_s]
+    csr = oracle.pattern(mesh.n_nodes, ln)
+    for _ in range(args.warmup):
+        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.mean(times)
+    value = n_s / (ms * 1e-3)
+    sample = f"first {n_s} of {mesh.n_elems} tets of the workload per step (all nodes), FP64, one host thread"
+    line = {
+        "impl": "reference", "metric": "tet elements assembled/s", "value": value, "unit": "elements/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "precision": "fp64 oracle", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU ---
+def time_steps(fn, steps, warmup, flush, stream):
+    """Per-step device time (ms) with an L2 flush before every step (not timed)."""
+    import torch
+
+    for _ in range(warmup):
+        flush()
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush()
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def max_sampled_error(asm, mesh, u_gpu_f64, out, rows):
+    """Row-scaled error of sampled rows against the oracle (full-size check)."""
+    import oracle
+
+    A, G, rhs = (t.double().cpu().numpy() for t in out)
+    rp, ci = (t.cpu().numpy() for t in asm.pattern())
+    ref = oracle.assemble_rows(mesh.coord, mesh.lnods, u_gpu_f64, rows, None, meshgen.RHO, meshgen.MU, meshgen.DT)
+    worst = 0.0
+    for r, (cols, a, g, rh) in zip(rows, ref):
+        s, e = rp[r], rp[r + 1]
+        assert np.array_equal(ci[s:e], cols)
+        worst = max(worst, np.abs(A[s:e] - a).max() / np.abs(a).max())
+        for d in range(3):
+            worst = max(worst, np.abs(G[d, s:e] - g[d]).max() / np.abs(g[d]).max())
+    return float(worst)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nsi.load_library()
+    mesh, u = meshgen.config_mesh(args.workload)
+    E, n = mesh.n_elems, mesh.n_nodes
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    results = {}
+    main_prec = args.precision
+    precs = [main_prec] + ([p for p in ("fp64", "mixed32", "mixed64") if p != main_prec] if not args.quick else [])
+    for prec in precs:
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec, scatter=args.scatter)
+        vt = torch.float64 if prec == "fp64" else torch.float32
+        ut = torch.as_tensor(u.T.copy()).to(dev, vt).contiguous()
+        out = asm.empty_outputs()
+        fn = lambda: asm.assemble(ut, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, out=out)  # noqa: E731
+        steps = args.steps if prec == main_prec else max(3, min(args.steps, 10))
+        sampler = ClockSampler(local) if prec == main_prec else None
+        if sampler:
+            sampler.start()
+        for _ in range(args.warmup):
+            flush()
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.mark("t0")
+        ms = time_steps(fn, steps, 0, flush, stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.mark("t1")
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        mean_ms = statistics.mean(ms)
+        rec = {"ms": mean_ms, "ms_min": min(ms), "ms_median": statistics.median(ms), "steps": steps,
+               "elements_per_s": E / (mean_ms * 1e-3), "clocks": clocks, "nnz": asm.nnz,
+               "mode": {0: "auto", 1: "color", 2: "atomic", 3: "gather"}[asm.scatter]}
+        if not args.quick or prec == main_prec:
+            rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(7).integers(0, n, 48)]))
+            uo = u if prec == "fp64" else u.astype(np.float32).astype(np.float64)
+            rec["max_rel_err"] = max_sampled_error(asm, mesh, uo, out, rows)
+            if prec != "fp64":
+                rec["max_rel_err_vs_f64_inputs"] = max_sampled_error(asm, mesh, u, out, rows)
+        if prec == main_prec and not args.no_e2e:
+            # end to end through the C ABI with host buffers
+            uh = torch.as_tensor(u.T.copy()).to(vt).pin_memory()
+            Ah = torch.empty(asm.nnz, dtype=asm.out_dtype).pin_memory()
+            Gh = torch.empty(3, asm.nnz, dtype=asm.out_dtype).pin_memory()
+            rh = torch.empty(3, n, dtype=asm.out_dtype).pin_memory()
+            asm.assemble_host(uh, Ah, Gh, rh, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
+            k_e2e = max(3, min(args.steps, 10))
+            barrier(world)
+            t = time.perf_counter()
+            for _ in range(k_e2e):
+                asm.assemble_host(uh, Ah, Gh, rh, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
+            e2e_s = (time.perf_counter() - t) / k_e2e
+            e2e_s = allreduce_max(e2e_s, world)
+            osz = Ah.element_size()
+            rec["e2e"] = {"value": world * E / e2e_s, "unit": "elements/s",
+                          "h2d_bytes_per_step": int(uh.numel() * uh.element_size()),
+                          "d2h_bytes_per_step": int(osz * (4 * asm.nnz + 3 * n)), "ms_per_step": 1e3 * e2e_s}
+        results[prec] = rec
+        asm.close()
+        del out
+
+    main = results[main_prec]
+    ms_max = allreduce_max(main["ms"], world)
+    value = world * E / (ms_max * 1e-3)
+    kernel = {"gather": "gather_kernel", "atomic": "elem_kernel", "color": "elem_kernel"}[main["mode"]]
+    bytes_alg = algorithmic_bytes(E, n, main["nnz"], main_prec)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    achieved = bytes_alg / (main["ms"] * 1e-3) / 1e9
+    line = {
+        "metric": "tet elements assembled/s", "value": value, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed64": "f32 (f64 output)", "mixed32": "f32"}[main_prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "precision": main_prec, "scatter": main["mode"],
+                   "elements": E, "nodes": n, "nnz": main["nnz"],
+                   "l2": "flushed (256 MiB write) before every timed step; working set > L2",
+                   "replicas": "each rank assembles its own copy of the workload" if world > 1 else None},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": read_traffic(kernel, args.workload, main_prec), "kernel": kernel,
+                     "algorithmic_bytes": bytes_alg, "peak_source": peak_src + " hbm_gbs (copy, burst)"},
+        "clocks": main["clocks"],
+        "gpu_launches": args.steps * 1 if main["mode"] != "color" else None,
+        "max_rel_err": main.get("max_rel_err"),
+        "max_rel_err_vs_f64_inputs": main.get("max_rel_err_vs_f64_inputs"),
+        "modes": {p: {k: r[k] for k in ("ms", "ms_min", "elements_per_s", "max_rel_err", "mode") if k in r}
+                  for p, r in results.items()},
+    }
+    if "fp64" in results and main_prec != "fp64":
+        line["speedup_vs_fp64"] = results["fp64"]["ms"] / main["ms"]
+    if "e2e" in main:
+        line["e2e"] = main["e2e"]
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = min(args.cpu_sample, E)
+        rate, med = cpu_oracle_rate(mesh, u, n_s)
+        line["cpu_baseline"] = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {n_s} tets of the workload (all nodes), FP64, median of 3 "
+                                          f"runs of {med:.2f} s each, one host thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube100", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="mixed64", choices=["fp64", "mixed64", "mixed32"])
+    ap.add_argument("--scatter", default="auto", choices=["auto", "gather", "color", "atomic"])
+    ap.add_argument("--cpu-sample", type=int, default=3_000_000)
+    ap.add_argument("--ref-sample", type=int, default=500_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="time only the main precision")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * nsi_assemble.h -- C ABI of the GB300 (sm_103a) incompressible-flow P1
+ * tetrahedral matrix assembly library (libnsi_assemble.so).
+ *
+ * The operation is the element matrix assembly of Alya's incompressible
+ * Navier-Stokes module (paper Section II-A, Listings 1 and 2): for every
+ * linear tetrahedron (4 nodes, 3 dimensions) gather nodal coordinates and
+ * velocities through the connectivity (calculate_transients), form the
+ * Jacobian, its determinant and inverse and the Cartesian shape-function
+ * gradients (calculate_cartesian_derivatives), integrate the convection,
+ * viscous and pressure-gradient terms at 4 Gauss points (Table I rows
+ * calculate_gauss_point_values ... calculate_viscous_term) and scatter-add
+ * the element matrices and right-hand side into global arrays
+ * (perform_assembly_in_global_system).  The per-term formulas are the
+ * Galerkin P1 form, because the paper names the subroutines but does not
+ * print their equations:
+ *
+ *   A_e[a][b]    = int rho N_a (u_h . grad N_b) + mu grad N_a . grad N_b
+ *                  + delta_ab rho |T_e| / (4 dt)            (4x4, scalar per node)
+ *   G_e[a][b][d] = - int d_d N_a N_b                        (4x4x3)
+ *   b_e[a][k]    = rho (|T_e| / 4) u^n_{a,k} / dt           (4x3, lumped)
+ *
+ * and A = sum_e A_e, G = sum_e G_e on one CSR pattern, rhs = sum_e b_e.
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers in NsiMesh, NsiFields and NsiOutputs are DEVICE
+ *    pointers unless the entry point says otherwise.  The caller owns every
+ *    input and output buffer and every stream; a handle owns only what it
+ *    builds at create time (CSR pattern, element colouring, gather maps,
+ *    packed coordinates) plus a device error word.
+ *  - Node arrays are structure-of-arrays, length n_nodes.  Connectivity is
+ *    int32 [n_elems][4], 0-based (Alya's lnods is 1-based Fortran; callers
+ *    subtract 1).  Every element must be positively oriented (det J > 0).
+ *  - CSR: row_ptr int32 [n_nodes + 1], col_idx int32 [nnz], columns strictly
+ *    ascending within a row: every node pair sharing an element (so the
+ *    diagonal of every node that belongs to an element; a node in no element
+ *    has an empty row and a zero right-hand side).  A_val is [nnz]; G_val is
+ *    component-major [3][nnz]; rhs is component-major [3][n_nodes].
+ *  - Precision (fixed per handle):
+ *      NSI_FP64            u, u_n: double;  A, G, rhs: double.  All element
+ *                          arithmetic and accumulation in IEEE double.
+ *      NSI_MIXED_F32_ACC64 u, u_n: float;   A, G, rhs: double.  Gathers and
+ *                          element arithmetic in float (coordinates kept as
+ *                          float hi/lo pairs so edge vectors keep ~48 bits);
+ *                          sums accumulated as compensated float pairs
+ *                          (about 48 significant bits) and stored as double.
+ *      NSI_MIXED_F32_ACC32 u, u_n: float;   A, G, rhs: float.
+ *  - Outputs are OVERWRITTEN by every assemble call (the call defines every
+ *    entry; no prior zeroing is needed).
+ *  - nsi_assemble* never allocate device memory, never synchronise the
+ *    stream, and only enqueue work on the given stream; they may be captured
+ *    into a CUDA graph.  Errors detected on the device (only when the handle
+ *    was created with debug_checks) are reported by nsi_device_status().
+ *  - Every function returns an nsi_status; on failure nsi_last_error()
+ *    returns a human-readable message for the calling thread.  No C++
+ *    exception crosses this ABI.
+ */
+#ifndef NSI_ASSEMBLE_H
+#define NSI_ASSEMBLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NSI_ABI_VERSION 1
+
+typedef struct NsiHandle NsiHandle; /* opaque; one per mesh */
+
+typedef enum {
+    NSI_OK = 0,
+    NSI_ERR_INVALID_ARG = 1,   /* NULL pointer, negative size, bad enum, bad dt */
+    NSI_ERR_BAD_MESH = 2,      /* node index out of range or det J <= 0 */
+    NSI_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    NSI_ERR_OOM = 4,           /* device or host allocation failed */
+    NSI_ERR_UNSUPPORTED = 5,   /* option not available for this mesh/precision */
+    NSI_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    NSI_ERR_DEVICE_CHECK = 7   /* a device-side bounds check fired */
+} nsi_status;
+
+typedef enum {
+    NSI_FP64 = 0,
+    NSI_MIXED_F32_ACC64 = 1,
+    NSI_MIXED_F32_ACC32 = 2
+} nsi_precision;
+
+typedef enum {
+    NSI_SCATTER_AUTO = 0,     /* library choice (row gather when available) */
+    NSI_SCATTER_COLOR = 1,    /* element colouring, plain read-add-write, deterministic */
+    NSI_SCATTER_ATOMIC = 2,   /* one element per thread, global atomic adds */
+    NSI_SCATTER_GATHER = 3    /* one CSR row per thread, gathers its elements, writes once;
+                                 deterministic; rows of at most 32 entries */
+} nsi_scatter;
+
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_elems;
+    const int32_t* lnods; /* device int32 [n_elems][4], 0-based */
+    const double* x;      /* device double [n_nodes] */
+    const double* y;
+    const double* z;
+} NsiMesh;
+
+typedef struct {
+    int32_t precision;    /* nsi_precision */
+    int32_t scatter;      /* nsi_scatter: default mode of nsi_assemble for this handle */
+    int32_t block;        /* threads per block, 0 = library default */
+    int32_t debug_checks; /* 1: kernels bounds-check every index they load */
+    int32_t reserved[4];  /* must be 0 */
+} NsiOptions;
+
+typedef struct {
+    const void* u[3];   /* device velocity components [n_nodes], double or float by precision */
+    const void* u_n[3]; /* velocity entering the RHS; NULL entries mean "same as u" */
+    double rho;         /* density */
+    double mu;          /* dynamic viscosity */
+    double dt;          /* time step, > 0 */
+} NsiFields;
+
+typedef struct {
+    void* A_val; /* device [nnz], double or float by precision */
+    void* G_val; /* device [3][nnz] */
+    void* rhs;   /* device [3][n_nodes] */
+} NsiOutputs;
+
+/*
+ * Build a handle for one mesh: validates the connectivity (indices in range,
+ * every det J > 0, computed in double on the host), builds the CSR pattern of
+ * all node pairs sharing an element, the row-gather maps, a greedy element
+ * colouring and packed coordinate copies.  Synchronous; allocates device
+ * memory owned by the handle.  `stream` (a cudaStream_t, may be NULL) is used
+ * for the uploads.  On failure *out is NULL.
+ */
+nsi_status nsi_assemble_create(const NsiMesh* mesh, const NsiOptions* opts, void* stream,
+                               NsiHandle** out);
+
+/* Release a handle (NULL is allowed).  Synchronises the device first. */
+nsi_status nsi_assemble_destroy(NsiHandle* h);
+
+/*
+ * The handle's CSR pattern (device pointers owned by the handle, valid until
+ * destroy) and its sizes.  Any output pointer may be NULL.
+ */
+nsi_status nsi_csr_pattern(const NsiHandle* h, const int32_t** row_ptr, const int32_t** col_idx,
+                           int64_t* nnz);
+
+/*
+ * Copy the handle's CSR pattern into caller buffers (host or device;
+ * row_ptr: n_nodes + 1 entries, col_idx: nnz entries; either may be NULL).
+ * Enqueued on `stream`, which is then synchronised.
+ */
+nsi_status nsi_csr_pattern_copy(const NsiHandle* h, int32_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Sizes and facts about the handle: nodes, elements, nnz, colours, max row length. */
+typedef struct {
+    int64_t n_nodes, n_elems, nnz;
+    int32_t n_colors, max_row, precision, scatter;
+    int64_t device_bytes; /* device memory owned by the handle */
+} NsiInfo;
+nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
+
+/*
+ * Assemble A, G and rhs for the velocities in `f` (Section II-A, Listing 1)
+ * using the handle's default scatter mode.  Device pointers; enqueues on
+ * `stream`; overwrites every output entry.
+ */
+nsi_status nsi_assemble(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream);
+
+/* Same as nsi_assemble with an explicit scatter mode (nsi_scatter). */
+nsi_status nsi_assemble_mode(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t scatter,
+                             void* stream);
+
+/*
+ * Assemble `count` independent meshes in one launch (one persistent grid
+ * strides over every mesh's rows).  All handles must share one precision and
+ * support the row-gather mode; count <= NSI_MAX_BATCH.  Pointers are passed to
+ * the kernel by value, so the call is graph-capturable and allocates nothing.
+ */
+#define NSI_MAX_BATCH 128
+nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os,
+                                int32_t count, void* stream);
+
+/*
+ * Vector-Jacobian product of the assembled residual R(u, mu) = A(u) u - b
+ * (b held fixed):  grad_u[l][m] = sum_{i,k} w[k][i] dR[k][i]/du[l][m] and
+ * grad_mu = sum_{i,k} w[k][i] dR[k][i]/dmu.  Element geometry is recomputed
+ * (no element matrices are stored).  w, grad_u: device [3][n_nodes] in the
+ * handle's velocity type; grad_mu: device double scalar.  Both outputs are
+ * overwritten.
+ */
+nsi_status nsi_assemble_vjp(NsiHandle* h, const NsiFields* f, const void* w, void* grad_u,
+                            double* grad_mu, void* stream);
+
+/*
+ * Residual of the assembled system without forming the matrix:
+ * R[k][i] = sum_j A_ij u[k][j] - rhs[k][i] for the velocities in `f` (the
+ * quantity whose adjoint nsi_assemble_vjp computes).  r: device [3][n_nodes]
+ * in the handle's velocity type, overwritten.
+ */
+nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream);
+
+/*
+ * End-to-end variant for callers holding HOST arrays: copies u (and u_n) from
+ * host memory to handle-owned device staging, assembles, and copies A, G, rhs
+ * back to the host buffers in `o` (pinned memory recommended), all on
+ * `stream`, then synchronises it.  The first call allocates the staging
+ * buffers; later calls reuse them.
+ */
+nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOutputs* o_host,
+                             void* stream);
+
+/*
+ * Synchronise `stream` and read the handle's device error word: NSI_OK, or
+ * NSI_ERR_DEVICE_CHECK (bounds check fired; the word is then cleared).
+ */
+nsi_status nsi_device_status(NsiHandle* h, void* stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* nsi_last_error(void);
+
+/* NSI_ABI_VERSION of the loaded library. */
+int32_t nsi_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSI_ASSEMBLE_H */

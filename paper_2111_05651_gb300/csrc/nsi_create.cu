@@ -1,0 +1,405 @@
+// Host side of libnsi_assemble: mesh preparation at create time (validation,
+// CSR pattern, row-gather map, element colouring, packed coordinates), handle
+// lifetime and error reporting.  The per-call kernels live in nsi_kernels.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "nsi_internal.cuh"
+
+namespace nsi {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+nsi_status fail(nsi_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+nsi_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? NSI_ERR_OOM : NSI_ERR_CUDA;
+}
+
+// run fn(lo, hi) over [0, n) on up to hardware_concurrency threads
+static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  int64_t nt = std::min<int64_t>(hw, std::max<int64_t>(1, n / 65536));
+  if (nt <= 1) {
+    fn(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+    if (lo < hi) th.emplace_back(fn, lo, hi);
+  }
+  for (auto& x : th) x.join();
+}
+
+template <typename T>
+static nsi_status dev_upload(NsiHandle* h, T** dst, const T* src, size_t count, cudaStream_t s) {
+  size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+  NSI_CUDA(cudaMalloc((void**)dst, bytes));
+  h->device_bytes += (int64_t)bytes;
+  if (count) NSI_CUDA(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  return NSI_OK;
+}
+
+static void free_handle(NsiHandle* h) {
+  if (!h) return;
+  cudaFree(h->row_ptr);
+  cudaFree(h->col_idx);
+  cudaFree(h->lnods);
+  cudaFree(h->color_elems);
+  cudaFree(h->star_ptr);
+  cudaFree(h->star);
+  cudaFree(h->diag_pos);
+  cudaFree(h->xyz64);
+  cudaFree(h->xyz_hi);
+  cudaFree(h->xyz_lo);
+  cudaFree(h->err);
+  cudaFree(h->stage);
+  delete h;
+}
+
+// Mesh preparation ---------------------------------------------------------
+static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
+  const int64_t n = h->n, E = h->E;
+  std::vector<int32_t> ln(4 * E);
+  std::vector<double> X(n), Y(n), Z(n);
+  if (E) NSI_CUDA(cudaMemcpy(ln.data(), m->lnods, sizeof(int32_t) * 4 * E, cudaMemcpyDeviceToHost));
+  NSI_CUDA(cudaMemcpy(X.data(), m->x, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  NSI_CUDA(cudaMemcpy(Y.data(), m->y, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  NSI_CUDA(cudaMemcpy(Z.data(), m->z, sizeof(double) * n, cudaMemcpyDeviceToHost));
+
+  // 1. validate indices and orientation (det J > 0, in double)
+  std::atomic<int64_t> bad_index{-1}, bad_det{-1};
+  parallel_for(E, [&](int64_t lo, int64_t hi) {
+    for (int64_t e = lo; e < hi; ++e) {
+      const int32_t* v = &ln[4 * e];
+      bool ok = true;
+      for (int a = 0; a < 4; ++a) ok &= (v[a] >= 0 && v[a] < n);
+      if (!ok) {
+        int64_t exp = -1;
+        bad_index.compare_exchange_strong(exp, e);
+        continue;
+      }
+      V3<double> x0{X[v[0]], Y[v[0]], Z[v[0]]};
+      V3<double> d1 = sub(V3<double>{X[v[1]], Y[v[1]], Z[v[1]]}, x0);
+      V3<double> d2 = sub(V3<double>{X[v[2]], Y[v[2]], Z[v[2]]}, x0);
+      V3<double> d3 = sub(V3<double>{X[v[3]], Y[v[3]], Z[v[3]]}, x0);
+      double det = dot(d1, cross(d2, d3));
+      if (!(det > 0.0)) {
+        int64_t exp = -1;
+        bad_det.compare_exchange_strong(exp, e);
+      }
+    }
+  });
+  if (bad_index.load() >= 0)
+    return fail(NSI_ERR_BAD_MESH, "element " + std::to_string(bad_index.load()) + " has a node index outside [0, n_nodes)");
+  if (bad_det.load() >= 0)
+    return fail(NSI_ERR_BAD_MESH, "element " + std::to_string(bad_det.load()) + " is inverted or degenerate (det J <= 0)");
+
+  // 2. node -> element incidence (elements ascending per node)
+  std::vector<int64_t> inc_ptr(n + 1, 0);
+  for (int64_t t = 0; t < 4 * E; ++t) inc_ptr[ln[t] + 1]++;
+  for (int64_t i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
+  std::vector<int64_t> inc(4 * E);  // e * 4 + a
+  {
+    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < 4; ++a) inc[fill[ln[4 * e + a]]++] = e * 4 + a;
+  }
+
+  // 3. CSR pattern: row i = sorted set of nodes sharing an element with i
+  //    (node i itself included; a node in no element has an empty row)
+  std::vector<int64_t> row_len(n);
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    std::vector<int32_t> buf;
+    for (int64_t i = lo; i < hi; ++i) {
+      buf.clear();
+      for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
+        int64_t e = inc[t] >> 2;
+        for (int a = 0; a < 4; ++a) buf.push_back(ln[4 * e + a]);
+      }
+      std::sort(buf.begin(), buf.end());
+      row_len[i] = std::unique(buf.begin(), buf.end()) - buf.begin();
+    }
+  });
+  std::vector<int64_t> rp64(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) rp64[i + 1] = rp64[i] + row_len[i];
+  const int64_t nnz = rp64[n];
+  if (nnz > INT32_MAX) return fail(NSI_ERR_UNSUPPORTED, "nnz exceeds int32 CSR indices");
+  h->nnz = nnz;
+  std::vector<int32_t> row_ptr(n + 1), col(nnz);
+  for (int64_t i = 0; i <= n; ++i) row_ptr[i] = (int32_t)rp64[i];
+  int64_t max_row = 0;
+  for (int64_t i = 0; i < n; ++i) max_row = std::max(max_row, row_len[i]);
+  h->max_row = (int)max_row;
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    std::vector<int32_t> buf;
+    for (int64_t i = lo; i < hi; ++i) {
+      buf.clear();
+      for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
+        int64_t e = inc[t] >> 2;
+        for (int a = 0; a < 4; ++a) buf.push_back(ln[4 * e + a]);
+      }
+      std::sort(buf.begin(), buf.end());
+      int64_t k = std::unique(buf.begin(), buf.end()) - buf.begin();
+      std::copy(buf.begin(), buf.begin() + k, col.begin() + rp64[i]);
+    }
+  });
+
+  // 4. row-gather map (positions of the other three nodes in the row)
+  h->gather_ok = max_row <= STAR_MAX_ROW;
+  std::vector<int32_t> star_ptr(n + 1, 0);
+  std::vector<uint16_t> star;
+  std::vector<uint8_t> diag(n, 0);
+  if (h->gather_ok) {
+    if (inc_ptr[n] > INT32_MAX) return fail(NSI_ERR_UNSUPPORTED, "too many element-node incidences");
+    for (int64_t i = 0; i <= n; ++i) star_ptr[i] = (int32_t)inc_ptr[i];
+    star.resize(inc_ptr[n]);
+    // even permutations of (0,1,2,3) that bring vertex a to the front
+    static const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        const int32_t* c = &col[rp64[i]];
+        int64_t len = row_len[i];
+        auto pos = [&](int32_t j) { return (int)(std::lower_bound(c, c + len, j) - c); };
+        diag[i] = len ? (uint8_t)pos((int32_t)i) : 0;
+        for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
+          int64_t e = inc[t] >> 2;
+          int a = (int)(inc[t] & 3);
+          unsigned w = 0;
+          for (int m2 = 0; m2 < 3; ++m2) w |= (unsigned)pos(ln[4 * e + EVEN[a][m2]]) << (STAR_BITS * m2);
+          star[t] = (uint16_t)w;
+        }
+      }
+    });
+  }
+
+  // 5. greedy element colouring: no two elements of one colour share a node
+  std::vector<int32_t> color(E);
+  {
+    std::vector<uint64_t> used;  // per node, 64 colours per word, grown on demand
+    int words = 1;
+    used.assign(n, 0);
+    std::vector<std::vector<uint64_t>> extra;  // colours >= 64 (rare)
+    int ncol = 0;
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t* v = &ln[4 * e];
+      uint64_t m0 = used[v[0]] | used[v[1]] | used[v[2]] | used[v[3]];
+      int c = -1;
+      if (~m0) c = __builtin_ctzll(~m0);
+      else {
+        for (int w = 0; w < (int)extra.size() && c < 0; ++w) {
+          uint64_t mw = extra[w][v[0]] | extra[w][v[1]] | extra[w][v[2]] | extra[w][v[3]];
+          if (~mw) c = 64 * (w + 1) + __builtin_ctzll(~mw);
+        }
+        if (c < 0) {
+          extra.emplace_back(n, 0);
+          c = 64 * (int)extra.size();
+          words++;
+        }
+      }
+      color[e] = c;
+      ncol = std::max(ncol, c + 1);
+      for (int a = 0; a < 4; ++a) {
+        if (c < 64) used[v[a]] |= 1ull << c;
+        else extra[c / 64 - 1][v[a]] |= 1ull << (c % 64);
+      }
+    }
+    (void)words;
+    h->n_colors = ncol;
+  }
+  std::vector<int32_t> color_elems(E);
+  h->color_off.assign(h->n_colors + 1, 0);
+  for (int64_t e = 0; e < E; ++e) h->color_off[color[e] + 1]++;
+  for (int c = 0; c < h->n_colors; ++c) h->color_off[c + 1] += h->color_off[c];
+  {
+    std::vector<int64_t> fill(h->color_off.begin(), h->color_off.end() - 1);
+    for (int64_t e = 0; e < E; ++e) color_elems[fill[color[e]]++] = (int32_t)e;
+  }
+
+  // 6. packed coordinates
+  std::vector<D4> xyz64;
+  std::vector<float4> xhi, xlo;
+  if (h->precision == NSI_FP64) {
+    xyz64.resize(n);
+    for (int64_t i = 0; i < n; ++i) xyz64[i] = D4{X[i], Y[i], Z[i], 0.0};
+  } else {
+    xhi.resize(n);
+    xlo.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+      float hx = (float)X[i], hy = (float)Y[i], hz = (float)Z[i];
+      xhi[i] = make_float4(hx, hy, hz, 0.0f);
+      xlo[i] = make_float4((float)(X[i] - hx), (float)(Y[i] - hy), (float)(Z[i] - hz), 0.0f);
+    }
+  }
+
+  // 7. gather launch plan: largest rows-per-block whose entries fit the budget
+  {
+    const int bytes_per_entry = (h->precision == NSI_FP64) ? 80 : (h->precision == NSI_MIXED_F32_ACC64 ? 56 : 40);
+    const int budget = 110 * 1024;
+    int chosen = 0, chosen_max = 0;
+    for (int R : {128, 64, 32}) {
+      int64_t mx = 0;
+      for (int64_t r0 = 0; r0 < n; r0 += R) mx = std::max<int64_t>(mx, rp64[std::min(n, r0 + R)] - rp64[r0]);
+      if (mx * bytes_per_entry <= budget) {
+        chosen = R;
+        chosen_max = (int)mx;
+        break;
+      }
+    }
+    if (chosen == 0) h->gather_ok = false;
+    h->plan.rows_per_block = chosen;
+    h->plan.max_block_entries = chosen_max;
+    h->plan.n_blocks = chosen ? (n + chosen - 1) / chosen : 0;
+  }
+
+  // 8. upload
+  nsi_status st;
+  if ((st = dev_upload(h, &h->row_ptr, row_ptr.data(), n + 1, s))) return st;
+  if ((st = dev_upload(h, &h->col_idx, col.data(), nnz, s))) return st;
+  if ((st = dev_upload(h, &h->lnods, reinterpret_cast<const int4*>(ln.data()), E, s))) return st;
+  if ((st = dev_upload(h, &h->color_elems, color_elems.data(), E, s))) return st;
+  if (h->gather_ok) {
+    if ((st = dev_upload(h, &h->star_ptr, star_ptr.data(), n + 1, s))) return st;
+    if ((st = dev_upload(h, &h->star, star.data(), star.size(), s))) return st;
+    if ((st = dev_upload(h, &h->diag_pos, diag.data(), n, s))) return st;
+  }
+  if (h->precision == NSI_FP64) {
+    if ((st = dev_upload(h, &h->xyz64, xyz64.data(), n, s))) return st;
+  } else {
+    if ((st = dev_upload(h, &h->xyz_hi, xhi.data(), n, s))) return st;
+    if ((st = dev_upload(h, &h->xyz_lo, xlo.data(), n, s))) return st;
+  }
+  NSI_CUDA(cudaMalloc((void**)&h->err, sizeof(unsigned)));
+  NSI_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), s));
+  NSI_CUDA(cudaStreamSynchronize(s));  // host vectors die at return
+  return NSI_OK;
+}
+
+}  // namespace nsi
+
+using namespace nsi;
+
+extern "C" {
+
+int32_t nsi_abi_version(void) { return NSI_ABI_VERSION; }
+
+const char* nsi_last_error(void) { return g_last_error.c_str(); }
+
+nsi_status nsi_assemble_create(const NsiMesh* mesh, const NsiOptions* opts, void* stream, NsiHandle** out) {
+  if (!out) return fail(NSI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !opts) return fail(NSI_ERR_INVALID_ARG, "mesh or opts is NULL");
+  if (mesh->n_nodes <= 0 || mesh->n_elems < 0) return fail(NSI_ERR_INVALID_ARG, "n_nodes must be > 0 and n_elems >= 0");
+  if (mesh->n_nodes > INT32_MAX || mesh->n_elems > INT32_MAX)
+    return fail(NSI_ERR_UNSUPPORTED, "more than 2^31-1 nodes or elements");
+  if (!mesh->x || !mesh->y || !mesh->z || (mesh->n_elems > 0 && !mesh->lnods))
+    return fail(NSI_ERR_INVALID_ARG, "mesh array pointer is NULL");
+  if (opts->precision < NSI_FP64 || opts->precision > NSI_MIXED_F32_ACC32)
+    return fail(NSI_ERR_INVALID_ARG, "unknown precision");
+  if (opts->scatter < NSI_SCATTER_AUTO || opts->scatter > NSI_SCATTER_GATHER)
+    return fail(NSI_ERR_INVALID_ARG, "unknown scatter mode");
+  if (opts->block < 0 || opts->block > 1024 || (opts->block % 32) != 0)
+    return fail(NSI_ERR_INVALID_ARG, "block must be 0 or a multiple of 32 up to 1024");
+  for (int r : opts->reserved)
+    if (r != 0) return fail(NSI_ERR_INVALID_ARG, "reserved option fields must be 0");
+
+  NsiHandle* h = new (std::nothrow) NsiHandle();
+  if (!h) return fail(NSI_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&h->device);
+  h->n = mesh->n_nodes;
+  h->E = mesh->n_elems;
+  h->precision = opts->precision;
+  h->scatter = opts->scatter;
+  h->block = opts->block ? opts->block : 256;
+  h->debug = opts->debug_checks != 0;
+  nsi_status st;
+  try {
+    st = build(h, mesh, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    st = fail(NSI_ERR_OOM, "host allocation failed while building the mesh maps");
+  } catch (const std::exception& ex) {
+    st = fail(NSI_ERR_CUDA, std::string("unexpected error: ") + ex.what());
+  }
+  if (st == NSI_OK && h->scatter == NSI_SCATTER_GATHER && !h->gather_ok) {
+    st = fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
+  }
+  if (st != NSI_OK) {
+    free_handle(h);
+    return st;
+  }
+  *out = h;
+  return NSI_OK;
+}
+
+nsi_status nsi_assemble_destroy(NsiHandle* h) {
+  if (!h) return NSI_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_handle(h);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize in destroy");
+  return NSI_OK;
+}
+
+nsi_status nsi_csr_pattern(const NsiHandle* h, const int32_t** row_ptr, const int32_t** col_idx, int64_t* nnz) {
+  if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
+  if (row_ptr) *row_ptr = h->row_ptr;
+  if (col_idx) *col_idx = h->col_idx;
+  if (nnz) *nnz = h->nnz;
+  return NSI_OK;
+}
+
+nsi_status nsi_csr_pattern_copy(const NsiHandle* h, int32_t* row_ptr, int32_t* col_idx, void* stream) {
+  if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (row_ptr) NSI_CUDA(cudaMemcpyAsync(row_ptr, h->row_ptr, sizeof(int32_t) * (h->n + 1), cudaMemcpyDefault, s));
+  if (col_idx) NSI_CUDA(cudaMemcpyAsync(col_idx, h->col_idx, sizeof(int32_t) * h->nnz, cudaMemcpyDefault, s));
+  NSI_CUDA(cudaStreamSynchronize(s));
+  return NSI_OK;
+}
+
+nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
+  if (!h || !info) return fail(NSI_ERR_INVALID_ARG, "handle or info is NULL");
+  info->n_nodes = h->n;
+  info->n_elems = h->E;
+  info->nnz = h->nnz;
+  info->n_colors = h->n_colors;
+  info->max_row = h->max_row;
+  info->precision = h->precision;
+  info->scatter = h->scatter;
+  info->device_bytes = h->device_bytes;
+  return NSI_OK;
+}
+
+nsi_status nsi_device_status(NsiHandle* h, void* stream) {
+  if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned word = 0;
+  NSI_CUDA(cudaMemcpyAsync(&word, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  NSI_CUDA(cudaStreamSynchronize(s));
+  if (word) {
+    NSI_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), s));
+    NSI_CUDA(cudaStreamSynchronize(s));
+    char buf[96];
+    snprintf(buf, sizeof buf, "device bounds check fired (error word 0x%x)", word);
+    return fail(NSI_ERR_DEVICE_CHECK, buf);
+  }
+  return NSI_OK;
+}
+
+}  // extern "C"

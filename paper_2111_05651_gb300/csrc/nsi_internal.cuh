@@ -1,0 +1,182 @@
+// Internal declarations of libnsi_assemble: the handle, status helpers and the
+// per-element arithmetic shared by the kernels.  Nothing here is part of the
+// public ABI (include/nsi_assemble.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nsi_assemble.h"
+
+namespace nsi {
+
+// ---------------------------------------------------------------- status ---
+void set_error(const std::string& msg);
+nsi_status fail(nsi_status s, const std::string& msg);
+nsi_status cuda_fail(cudaError_t e, const char* what);
+
+#define NSI_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return nsi::cuda_fail(e_, #call); \
+  } while (0)
+
+// device error word bits (set by kernels built with debug checks)
+enum : unsigned { ERR_BAD_INDEX = 1u, ERR_NOT_IN_PATTERN = 2u, ERR_STAR = 4u };
+
+// Row-gather ("pull") map: for CSR row i, one 16-bit word per element that
+// contains node i, in increasing element order: the positions, inside row i's
+// column list, of the element's other three nodes (5 bits each), ordered so
+// that (i, j1, j2, j3) is an even permutation of the element's node order
+// (hence a positively oriented tet).  Rows longer than 32 entries cannot be
+// encoded; such meshes do not support the gather mode.
+constexpr int STAR_BITS = 5;
+constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
+
+// vector types with explicit alignment (CUDA 13 deprecates the unsuffixed double4)
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+struct GatherPlan {
+  int rows_per_block = 0;   // threads per block = rows per block
+  int max_block_entries = 0;  // max over blocks of the CSR entries of the block's rows
+  int64_t n_blocks = 0;
+};
+
+}  // namespace nsi
+
+struct NsiHandle {
+  int device = 0;
+  int64_t n = 0, E = 0, nnz = 0;
+  int precision = NSI_FP64;
+  int scatter = NSI_SCATTER_AUTO;
+  int block = 256;
+  int debug = 0;
+  int max_row = 0;
+  int n_colors = 0;
+  bool gather_ok = false;
+  int64_t device_bytes = 0;
+
+  // CSR pattern
+  int32_t* row_ptr = nullptr;  // [n+1]
+  int32_t* col_idx = nullptr;  // [nnz]
+  // connectivity copy and colouring
+  int4* lnods = nullptr;        // [E]
+  int32_t* color_elems = nullptr;  // [E] element ids grouped by colour
+  std::vector<int64_t> color_off;  // host [n_colors + 1]
+  // row-gather map
+  int32_t* star_ptr = nullptr;  // [n+1]
+  uint16_t* star = nullptr;     // [star_ptr[n]]
+  uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row
+  nsi::GatherPlan plan;
+  // coordinates: double4 for FP64, float4 hi + float4 lo for the mixed modes
+  nsi::D4* xyz64 = nullptr;
+  float4* xyz_hi = nullptr;
+  float4* xyz_lo = nullptr;
+  // device error word
+  unsigned* err = nullptr;
+  // staging for nsi_assemble_host (allocated on first use)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace nsi {
+
+// --------------------------------------------------- element arithmetic ---
+// For a positively oriented tet with edge vectors d1, d2, d3 leaving vertex 0,
+// the cofactor vectors c_b = det(J) grad N_b are
+//   c1 = d2 x d3,  c2 = d3 x d1,  c3 = d1 x d2,  c0 = -(c1 + c2 + c3),
+// det J = d1 . c1 and |T| = det J / 6.  With them the Galerkin P1 terms are
+//   convection  rho int N_a (u_h . grad N_b) = rho/120 (S + u_a) . c_b,
+//               S = sum_c u_c  (exact P1 mass moments int N_a N_c = |T|(1+d_ac)/20,
+//               which the 4-point Gauss rule integrates exactly)
+//   viscous     mu |T| grad N_a . grad N_b  = mu / (6 det) c_a . c_b
+//   lumped mass rho |T| / (4 dt)            = rho det / (24 dt)
+//   pressure gradient  -int d_d N_a N_b     = -c_a[d] / 24  (every b)
+//   lumped RHS  rho |T| u^n_a / (4 dt)      = rho det / (24 dt) u^n_a
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+template <typename T>
+__host__ __device__ __forceinline__ V3<T> cross(const V3<T>& a, const V3<T>& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T>
+__host__ __device__ __forceinline__ T dot(const V3<T>& a, const V3<T>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ V3<T> add(const V3<T>& a, const V3<T>& b) {
+  return {a.x + b.x, a.y + b.y, a.z + b.z};
+}
+template <typename T>
+__host__ __device__ __forceinline__ V3<T> sub(const V3<T>& a, const V3<T>& b) {
+  return {a.x - b.x, a.y - b.y, a.z - b.z};
+}
+
+// ------------------------------------------------ f32 -> f64 without DP ops ---
+// GB300 executes double-precision instructions (including conversions) at a
+// small fraction of the single-precision rate, so the mixed modes build their
+// double outputs from integer operations on the IEEE-754 bit patterns.
+
+// Exact float -> double (every float is a double).  Subnormal floats are
+// renormalised; inf/nan keep their class.
+__device__ __forceinline__ long long f32_to_f64_bits(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned sign = u & 0x80000000u;
+  unsigned e = (u >> 23) & 0xffu;
+  unsigned m = u & 0x7fffffu;
+  unsigned e64;
+  if (e == 0u) {
+    if (m == 0u) return (long long)((unsigned long long)sign << 32);
+    int lz = __clz(m) - 8;  // shift that brings the leading 1 to bit 23
+    m = (m << lz) & 0x7fffffu;
+    e64 = 897u - (unsigned)lz;  // 1 - 127 + 1023 - lz
+  } else if (e == 0xffu) {
+    e64 = 0x7ffu;
+  } else {
+    e64 = e + 896u;  // 1023 - 127
+  }
+  unsigned hi = sign | (e64 << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  return (long long)(((unsigned long long)hi << 32) | lo);
+}
+
+// double nearest to hi + lo for a compensated pair with |lo| <= ulp_float(hi)
+// (the result of TwoSum accumulation): the double bits of hi plus lo expressed
+// in units of hi's double ulp (2^(e_hi - 179) for a normal float hi), rounded
+// to nearest (one double ulp at most).  Finite inputs only.
+__device__ __forceinline__ long long pair_to_f64_bits(float hi, float lo) {
+  if (hi == 0.0f) return f32_to_f64_bits(lo);
+  long long bits = f32_to_f64_bits(hi);
+  unsigned uh = __float_as_uint(hi);
+  unsigned eh = (uh >> 23) & 0xffu;
+  unsigned ul = __float_as_uint(lo);
+  unsigned el = (ul >> 23) & 0xffu;
+  if (el == 0u || eh == 0u) return bits;  // lo zero/subnormal, or hi subnormal: lo below resolution
+  // scale lo by 2^(179 - eh) through its exponent field: el' = el + 179 - eh
+  int el2 = (int)el + 179 - (int)eh;
+  if (el2 <= 0) return bits;                      // below half an ulp
+  if (el2 >= 127 + 30) return bits;               // not a normalised pair; ignore
+  float scaled = __uint_as_float((ul & 0x807fffffu) | ((unsigned)el2 << 23));
+  int k = __float2int_rn(scaled);
+  // hi an exact power of two and lo of opposite sign: the sum lies in the binade
+  // below, whose ulp is half as large
+  if ((uh & 0x7fffffu) == 0u && ((uh ^ ul) & 0x80000000u)) k *= 2;
+  // hi's sign decides the direction of the integer step on the magnitude bits
+  return (uh & 0x80000000u) ? bits - (long long)k : bits + (long long)k;
+}
+
+// error-free sum: s + e == a + b exactly (Knuth's TwoSum, 6 float ops)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+}  // namespace nsi

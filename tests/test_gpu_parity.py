@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Bars: CSR pattern bit-exact; FP64 mode within 1e-12 row-scaled error; mixed
+modes within 1e-5 (the benchmark spec's tolerances), both against the oracle fed
+the exact inputs the kernels see (mixed modes receive float32 velocities, so
+the oracle is run on those values promoted to float64) and, for the mixed
+modes, also against the oracle on the original float64 velocities.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from tests._common import errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+nsi = pytest.importorskip("paper_2111_05651_gb300")
+
+TOL = {"fp64": 1e-12, "mixed64": 1e-5, "mixed32": 1e-5}
+RHO, MU, DT = meshgen.RHO, meshgen.MU, meshgen.DT
+
+
+def _run(mesh, u, precision, scatter, un=None, rho=RHO, mu=MU, dt=DT, debug=False):
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter=scatter, debug_checks=debug)
+    ut = torch.as_tensor(u.T.copy())
+    unt = torch.as_tensor(un.T.copy()) if un is not None else None
+    A, G, rhs = asm.assemble(ut, unt, rho=rho, mu=mu, dt=dt)
+    torch.cuda.synchronize()
+    if debug:
+        asm.device_status()
+    rp, ci = asm.pattern()
+    res = (rp.cpu().numpy(), ci.cpu().numpy(), A.double().cpu().numpy(), G.double().cpu().numpy(),
+           rhs.double().cpu().numpy())
+    asm.close()
+    return res
+
+
+def _oracle(mesh, u, precision, un=None, rho=RHO, mu=MU, dt=DT):
+    if precision != "fp64":
+        u = u.astype(np.float32).astype(np.float64)
+        un = None if un is None else un.astype(np.float32).astype(np.float64)
+    return oracle.assemble(mesh.coord, mesh.lnods, u, un, rho, mu, dt)
+
+
+CASES = [
+    ("cube8", dict(name="cube8")),
+    ("cube6_jit_random", dict(N=6, jitter=0.15, numbering="random", seed=31)),
+    ("cube7_jit_rcm", dict(N=7, jitter=0.15, numbering="rcm", seed=32, noise=0.05)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("scatter", ["gather", "color", "atomic"])
+def test_parity_vs_oracle(case, precision, scatter):
+    name, kw = case
+    mesh, u = meshgen.config_mesh(**kw) if "name" not in kw else meshgen.config_mesh(kw["name"])
+    rp, ci, A, G, rhs = _run(mesh, u, precision, scatter)
+    orp, oci, oA, oG, orhs = _oracle(mesh, u, precision)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(ci, oci)
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], err
+    if precision != "fp64":
+        # also against the unrounded float64 velocities
+        _, _, fA, fG, frhs = oracle.assemble(mesh.coord, mesh.lnods, u, None, RHO, MU, DT)
+        err2 = errors(rp, A, G, rhs, fA, fG, frhs)
+        assert max(err2.values()) <= TOL[precision], err2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64"])
+def test_separate_rhs_velocity(precision):
+    mesh, u = meshgen.config_mesh(N=5, jitter=0.1, numbering="random", seed=40)
+    un = np.random.default_rng(41).standard_normal(u.shape)
+    rp, ci, A, G, rhs = _run(mesh, u, precision, "gather", un=un, rho=1.3, mu=0.02, dt=0.05)
+    _, _, oA, oG, orhs = _oracle(mesh, u, precision, un=un, rho=1.3, mu=0.02, dt=0.05)
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("scatter", ["gather", "color"])
+def test_deterministic_bitwise(precision, scatter):
+    """Gather and colour scatter are run-to-run bit-reproducible."""
+    mesh, u = meshgen.config_mesh(N=9, jitter=0.15, numbering="random", seed=42)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter=scatter)
+    ut = torch.as_tensor(u.T.copy())
+    r1 = [t.clone() for t in asm.assemble(ut)]
+    r2 = asm.assemble(ut)
+    torch.cuda.synchronize()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+
+
+def test_single_tet_and_isolated_node():
+    coord = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [5, 5, 5]], dtype=float)
+    lnods = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    u = np.random.default_rng(3).standard_normal((5, 3))
+    mesh = meshgen.Mesh(coord=coord, lnods=lnods)
+    for precision in ["fp64", "mixed64", "mixed32"]:
+        for scatter in ["gather", "color", "atomic"]:
+            rp, ci, A, G, rhs = _run(mesh, u, precision, scatter)
+            orp, oci, oA, oG, orhs = _oracle(mesh, u, precision)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(ci, oci)
+            assert rp[4] == rp[5]                  # isolated node: empty row
+            assert np.all(rhs[:, 4] == 0)
+            err = errors(rp, A, G, rhs, oA, oG, orhs)
+            assert max(err.values()) <= TOL[precision], (precision, scatter, err)
+
+
+def test_ragged_row_blocks():
+    """n not a multiple of the rows-per-block and rows of uneven length (boundary)."""
+    mesh, u = meshgen.config_mesh(N=11, jitter=0.15, numbering="random", seed=43)
+    assert mesh.n_nodes % 128 != 0
+    rp, ci, A, G, rhs = _run(mesh, u, "mixed64", "gather")
+    _, _, oA, oG, orhs = _oracle(mesh, u, "mixed64")
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= 1e-5, err
+
+
+def test_debug_checks_clean():
+    mesh, u = meshgen.config_mesh(N=5, jitter=0.1, numbering="random", seed=44)
+    for precision in ["fp64", "mixed64"]:
+        for scatter in ["gather", "color", "atomic"]:
+            rp, ci, A, G, rhs = _run(mesh, u, precision, scatter, debug=True)
+            _, _, oA, oG, orhs = _oracle(mesh, u, precision)
+            err = errors(rp, A, G, rhs, oA, oG, orhs)
+            assert max(err.values()) <= TOL[precision]
+
+
+def test_batched_equals_single():
+    meshes = [meshgen.config_mesh(N=n, jitter=0.15, numbering="natural", seed=50 + n) for n in (3, 7, 5)]
+    asms = [nsi.Assembler(m.coord, m.lnods, precision="mixed64") for m, _ in meshes]
+    us = [torch.as_tensor(u.T.copy()) for _, u in meshes]
+    singles = [[t.clone() for t in a.assemble(u)] for a, u in zip(asms, us)]
+    batched = nsi.assemble_batched(asms, us)
+    torch.cuda.synchronize()
+    for s, b in zip(singles, batched):
+        for x, y in zip(s, b):
+            assert torch.equal(x, y)
+
+
+def test_host_end_to_end_matches_device():
+    mesh, u = meshgen.config_mesh(N=6, jitter=0.15, numbering="random", seed=45)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="mixed64")
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = asm.assemble(ut)
+    uh = ut.float().pin_memory()
+    Ah = torch.empty(asm.nnz, dtype=torch.float64).pin_memory()
+    Gh = torch.empty(3, asm.nnz, dtype=torch.float64).pin_memory()
+    rh = torch.empty(3, asm.n, dtype=torch.float64).pin_memory()
+    asm.assemble_host(uh, Ah, Gh, rh)
+    assert torch.equal(A.cpu(), Ah)
+    assert torch.equal(G.cpu(), Gh)
+    assert torch.equal(rhs.cpu(), rh)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64"])
+def test_residual_matches_oracle(precision):
+    mesh, u = meshgen.config_mesh(N=5, jitter=0.15, numbering="random", seed=46)
+    un = np.random.default_rng(2).standard_normal(u.shape)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    R = asm.residual(torch.as_tensor(u.T.copy()), u_n=torch.as_tensor(un.T.copy())).double().cpu().numpy()
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    uno = un if precision == "fp64" else un.astype(np.float32).astype(np.float64)
+    rp, ci, oA, oG, orhs = oracle.assemble(mesh.coord, mesh.lnods, uo, uno)
+    Ro = oracle.residual((rp, ci, oA), orhs.T, uo)   # [n, 3]
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    scale = np.abs(Ro).max()
+    assert np.abs(R.T - Ro).max() <= tol * scale * 10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64"])
+def test_vjp_matches_oracle(precision):
+    mesh, u = meshgen.config_mesh(N=6, jitter=0.15, numbering="random", seed=47)
+    w = np.random.default_rng(40).standard_normal(u.shape)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    gu, gmu = asm.vjp(torch.as_tensor(u.T.copy()), torch.as_tensor(w.T.copy()))
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    wo = w if precision == "fp64" else w.astype(np.float32).astype(np.float64)
+    ogu, ogmu = oracle.vjp(mesh.coord, mesh.lnods, uo, wo, RHO, MU, DT)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    gu = gu.double().cpu().numpy().T
+    assert np.abs(gu - ogu).max() <= tol * np.abs(ogu).max()
+    assert abs(float(gmu.item()) - ogmu) <= tol * max(abs(ogmu), 1e-30) * 10
+
+
+def test_autograd_residual():
+    mesh, u = meshgen.config_mesh(N=4, jitter=0.15, numbering="natural", seed=48)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="fp64")
+    ut = torch.as_tensor(u.T.copy()).cuda().requires_grad_(True)
+    mu = torch.tensor(0.01, dtype=torch.float64, requires_grad=True)
+    w = torch.randn(3, mesh.n_nodes, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    R = nsi.NsiResidual.apply(ut, mu, asm, 1.0, 0.01)
+    (R * w).sum().backward()
+    ogu, ogmu = oracle.vjp(mesh.coord, mesh.lnods, u, w.cpu().numpy().T, 1.0, 0.01, 0.01)
+    assert np.abs(ut.grad.cpu().numpy().T - ogu).max() <= 1e-12 * np.abs(ogu).max()
+    assert mu.grad.item() == pytest.approx(ogmu, rel=1e-11)
+
+
+def test_bad_meshes_rejected():
+    coord = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    with pytest.raises(nsi.NsiError) as ex:
+        nsi.Assembler(coord, np.array([[0, 1, 3, 2]], dtype=np.int32))     # inverted
+    assert ex.value.status == nsi.NSI_ERR_BAD_MESH
+    with pytest.raises(nsi.NsiError) as ex:
+        nsi.Assembler(coord, np.array([[0, 1, 2, 4]], dtype=np.int32))     # out of range
+    assert ex.value.status == nsi.NSI_ERR_BAD_MESH
+    with pytest.raises(nsi.NsiError) as ex:
+        nsi.Assembler(coord, np.array([[0, 1, 2, 2]], dtype=np.int32))     # degenerate
+    assert ex.value.status == nsi.NSI_ERR_BAD_MESH
