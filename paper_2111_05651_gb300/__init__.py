@@ -250,6 +250,7 @@ class Assembler:
         with torch.cuda.device(self.device):
             self.handle = nsi_assemble_create(mesh, opts, _stream_ptr(stream))
         info = nsi_info(self.handle)
+        self.scatter = info.scatter  # the handle's default mode, resolved by the library
         self.n, self.E, self.nnz = info.n_nodes, info.n_elems, info.nnz
         self.n_colors, self.max_row, self.device_bytes = info.n_colors, info.max_row, info.device_bytes
         self._pattern = None

@@ -251,21 +251,35 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
 
   // 7. gather launch plan: largest rows-per-block whose entries fit the budget
   {
-    const int bytes_per_entry = (h->precision == NSI_FP64) ? 80 : (h->precision == NSI_MIXED_F32_ACC64 ? 56 : 40);
-    const int budget = 110 * 1024;
-    int chosen = 0, chosen_max = 0;
-    for (int R : {128, 64, 32}) {
-      int64_t mx = 0;
-      for (int64_t r0 = 0; r0 < n; r0 += R) mx = std::max<int64_t>(mx, rp64[std::min(n, r0 + R)] - rp64[r0]);
-      if (mx * bytes_per_entry <= budget) {
+    // rows per block chosen for the most resident warps per SM (shared memory
+    // of the block's layout, the kernel's registers, 2048 threads per SM)
+    const size_t smem_sm = 228 * 1024, smem_max = 200 * 1024;
+    const int regs = std::max(32, gather_kernel_regs(h->precision));
+    const int W = std::max(1, (int)max_row);
+    int chosen = 0, chosen_L = 0, chosen_S = 0, best_warps = 0;
+    for (int R : {128, 96, 64, 32}) {
+      int64_t mL = 0, mS = 0;
+      for (int64_t r0 = 0; r0 < n; r0 += R) {
+        const int64_t r1 = std::min(n, r0 + R);
+        mL = std::max<int64_t>(mL, rp64[r1] - rp64[r0]);
+        mS = std::max<int64_t>(mS, inc_ptr[r1] - inc_ptr[r0]);
+      }
+      const size_t sm = gather_smem(h->precision, R, W, (int)mL, (int)mS).total();
+      if (sm > smem_max) continue;
+      int blocks = (int)std::min<size_t>({smem_sm / (sm + 1024), (size_t)32, (size_t)(2048 / R),
+                                          (size_t)(65536 / (R * regs))});
+      const int warps = blocks * R / 32;
+      if (warps > best_warps) {
+        best_warps = warps;
         chosen = R;
-        chosen_max = (int)mx;
-        break;
+        chosen_L = (int)mL;
+        chosen_S = (int)mS;
       }
     }
     if (chosen == 0) h->gather_ok = false;
     h->plan.rows_per_block = chosen;
-    h->plan.max_block_entries = chosen_max;
+    h->plan.max_block_entries = chosen_L;
+    h->plan.max_block_stars = chosen_S;
     h->plan.n_blocks = chosen ? (n + chosen - 1) / chosen : 0;
   }
 
@@ -340,6 +354,9 @@ nsi_status nsi_assemble_create(const NsiMesh* mesh, const NsiOptions* opts, void
   if (st == NSI_OK && h->scatter == NSI_SCATTER_GATHER && !h->gather_ok) {
     st = fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
   }
+  // the default mode: row gather where the mesh allows it (rows <= 32 entries)
+  if (st == NSI_OK && h->scatter == NSI_SCATTER_AUTO)
+    h->scatter = h->gather_ok ? NSI_SCATTER_GATHER : NSI_SCATTER_ATOMIC;
   if (st != NSI_OK) {
     free_handle(h);
     return st;

@@ -42,10 +42,52 @@ struct alignas(32) D4 {
 };
 
 struct GatherPlan {
-  int rows_per_block = 0;   // threads per block = rows per block
+  int rows_per_block = 0;     // threads per block = rows per block
   int max_block_entries = 0;  // max over blocks of the CSR entries of the block's rows
+  int max_block_stars = 0;    // max over blocks of the row-gather words of the block's rows
   int64_t n_blocks = 0;
 };
+
+// Shared-memory layout of one row-gather block: R rows (one per thread), W
+// slots per row (the longest row of the mesh), L CSR entries and S row-gather
+// words.  Slot q of row t lives at index q * R + t ("thread-interleaved"), so
+// the lanes of a warp touch consecutive records whichever slot each lane
+// uses: the element loop is free of shared-memory bank conflicts.
+//   nb0   T[4] per slot: edge vector d = x_j - x_i and u_x of the neighbour
+//   nb1   T[2] per slot: u_y, u_z
+//   acc   accumulators per slot (ab bytes): A and the three sums of c_i
+//   rawux float per slot (single-accumulator float mode only; the other
+//         modes stage u_x inside acc)
+//   col   int32 per CSR entry, erow uint8 per CSR entry (its row), lb int32
+//         per row (row start inside the block's CSR range), star uint16 per word
+// Used identically by the host (launch size) and the kernel (carving).
+struct GatherSmem {
+  int R, W, L, S, tb, ab;
+  __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+  __host__ __device__ size_t N() const { return (size_t)R * W; }
+  __host__ __device__ size_t nb0() const { return 0; }
+  __host__ __device__ size_t nb1() const { return up16(nb0() + (size_t)4 * tb * N()); }
+  __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
+  __host__ __device__ size_t rawux() const { return up16(acc() + (size_t)ab * N()); }
+  __host__ __device__ size_t col() const { return up16(rawux() + (ab == 16 ? (size_t)4 * N() : 0)); }
+  __host__ __device__ size_t erow() const { return up16(col() + (size_t)4 * L); }
+  __host__ __device__ size_t lb() const { return up16(erow() + (size_t)L); }
+  __host__ __device__ size_t star() const { return up16(lb() + (size_t)4 * R); }
+  __host__ __device__ size_t total() const { return up16(star() + (size_t)2 * S); }
+};
+
+__host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S) {
+  GatherSmem g;
+  g.R = R;
+  g.W = W;
+  g.L = L;
+  g.S = S;
+  g.tb = precision == NSI_FP64 ? 8 : 4;
+  g.ab = precision == NSI_MIXED_F32_ACC32 ? 16 : 32;
+  return g;
+}
+
+int gather_kernel_regs(int precision);  // registers per thread of the row-gather kernel
 
 }  // namespace nsi
 

@@ -138,6 +138,28 @@ __device__ __forceinline__ V3<T> load_vec(const void* const* comp, int64_t v) {
           __ldg(static_cast<const T*>(comp[2]) + v)};
 }
 
+// asynchronous global -> shared copies (cp.async): many gathers in flight per
+// thread without holding registers
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 8) cp_async8(dst, src);
+  else cp_async4(dst, src);
+}
+
 // ------------------------------------------------ element-centric kernel ---
 template <typename T, typename Out>
 __device__ __forceinline__ void add_out(Out* p, T v, bool atomic);
@@ -235,7 +257,8 @@ __global__ void __launch_bounds__(256) elem_kernel(MeshView m, FieldView f, OutV
 }
 
 // ---------------------------------------------------- row-gather kernel ---
-// Accumulator of one output value: plain T, or a compensated float pair.
+// Register accumulator of one output value: plain T, or a compensated float
+// pair (TwoSum) for the mixed mode with double output.
 template <int P>
 struct Acc {
   using T = typename Prec<P>::T;
@@ -255,157 +278,430 @@ struct Acc<NSI_MIXED_F32_ACC64> {
   }
 };
 
-// shared-memory record of one CSR entry of the block: neighbour data (edge
-// vector from the row's node and the neighbour's velocity) and the 4
-// accumulators A, G_x, G_y, G_z of the entry
-template <int P>
-struct Entry {
-  using T = typename Prec<P>::T;
-  V3<T> d, u;
-  Acc<P> a[4];
-};
-
-template <int P>
-__host__ __device__ constexpr int entry_bytes() {
-  return (int)sizeof(Entry<P>);
-}
-
 __device__ __forceinline__ void store_acc(double* p, const Acc<NSI_FP64>& a) { *p = a.v; }
 __device__ __forceinline__ void store_acc(float* p, const Acc<NSI_MIXED_F32_ACC32>& a) { *p = a.v; }
 __device__ __forceinline__ void store_acc(double* p, const Acc<NSI_MIXED_F32_ACC64>& a) {
   // renormalise the pair (Fast2Sum) so that |lo| <= ulp(hi)/2, then build the double
-  float s = a.hi + a.lo;
-  float lo = a.lo - (s - a.hi);
+  const float s = a.hi + a.lo;
+  const float lo = a.lo - (s - a.hi);
   *reinterpret_cast<long long*>(p) = pair_to_f64_bits(s, lo);
+}
+
+template <typename T>
+struct alignas(4 * sizeof(T)) T4 {
+  T x, y, z, w;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) T2 {
+  T x, y;
+};
+
+// Accumulators of the block's slots in shared memory: the A value and the
+// unscaled pressure-gradient sums (sum of c_i) of each entry.  A slot is only
+// touched by the thread owning its row until the final write-out, so no
+// atomics are needed.  add3() updates three DISTINCT slots (the three other
+// nodes of one element sit at three different positions of the row), so all
+// three loads are issued before the stores.
+template <int P>
+struct AccSmem;
+template <>
+struct AccSmem<NSI_MIXED_F32_ACC32> {
+  float4* __restrict__ a;
+  __device__ __forceinline__ AccSmem(unsigned char* p, size_t) : a(reinterpret_cast<float4*>(p)) {}
+  __device__ __forceinline__ void zero(int k) { a[k] = make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ __forceinline__ void add3(int k1, int k2, int k3, float A1, float A2, float A3, float gx, float gy,
+                                       float gz) {
+    float4 v1 = a[k1], v2 = a[k2], v3 = a[k3];
+    v1.x += A1; v1.y += gx; v1.z += gy; v1.w += gz;
+    v2.x += A2; v2.y += gx; v2.z += gy; v2.w += gz;
+    v3.x += A3; v3.y += gx; v3.z += gy; v3.w += gz;
+    a[k1] = v1;
+    a[k2] = v2;
+    a[k3] = v3;
+  }
+  // sums over the row's slots t, t + R, ... (len of them) except slot kd
+  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>* r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      if (k == kd) continue;
+      const float4 v = a[k];
+      r[0].add(v.x); r[1].add(v.y); r[2].add(v.z); r[3].add(v.w);
+    }
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>* r) {
+    a[k] = make_float4(r[0].v, r[1].v, r[2].v, r[3].v);
+  }
+  __device__ __forceinline__ void write(int k, float kg, float* A, float* G, int64_t nnz, int64_t g) const {
+    const float4 v = a[k];
+    A[g] = v.x;
+    G[g] = kg * v.y;
+    G[nnz + g] = kg * v.z;
+    G[2 * nnz + g] = kg * v.w;
+  }
+};
+template <>
+struct AccSmem<NSI_MIXED_F32_ACC64> {
+  float4* __restrict__ hi;
+  float4* __restrict__ lo;
+  __device__ __forceinline__ AccSmem(unsigned char* p, size_t N)
+      : hi(reinterpret_cast<float4*>(p)), lo(reinterpret_cast<float4*>(p) + N) {}
+  __device__ __forceinline__ void zero(int k) {
+    hi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  static __device__ __forceinline__ void acc1(float& h, float& l, float x) {
+    float s, e;
+    two_sum(h, x, s, e);
+    h = s;
+    l += e;
+  }
+  static __device__ __forceinline__ void acc4(float4& h, float4& l, float A, float gx, float gy, float gz) {
+    acc1(h.x, l.x, A);
+    acc1(h.y, l.y, gx);
+    acc1(h.z, l.z, gy);
+    acc1(h.w, l.w, gz);
+  }
+  __device__ __forceinline__ void add3(int k1, int k2, int k3, float A1, float A2, float A3, float gx, float gy,
+                                       float gz) {
+    float4 h1 = hi[k1], h2 = hi[k2], h3 = hi[k3];
+    float4 l1 = lo[k1], l2 = lo[k2], l3 = lo[k3];
+    acc4(h1, l1, A1, gx, gy, gz);
+    acc4(h2, l2, A2, gx, gy, gz);
+    acc4(h3, l3, A3, gx, gy, gz);
+    hi[k1] = h1;
+    hi[k2] = h2;
+    hi[k3] = h3;
+    lo[k1] = l1;
+    lo[k2] = l2;
+    lo[k3] = l3;
+  }
+  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      if (k == kd) continue;
+      const float4 h = hi[k], l = lo[k];
+      r[0].add(h.x); r[1].add(h.y); r[2].add(h.z); r[3].add(h.w);
+      r[0].lo += l.x; r[1].lo += l.y; r[2].lo += l.z; r[3].lo += l.w;
+    }
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>* r) {
+    hi[k] = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
+    lo[k] = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
+  }
+  __device__ __forceinline__ void write(int k, float kg, double* A, double* G, int64_t nnz, int64_t g) const {
+    const float4 h = hi[k], l = lo[k];
+    Acc<NSI_MIXED_F32_ACC64> t;
+    t.hi = h.x; t.lo = l.x; store_acc(A + g, t);
+    // kg * (hi + lo), keeping the product error of the leading part
+    float p;
+    p = kg * h.y; t.hi = p; t.lo = fmaf(kg, h.y, -p) + kg * l.y; store_acc(G + g, t);
+    p = kg * h.z; t.hi = p; t.lo = fmaf(kg, h.z, -p) + kg * l.z; store_acc(G + nnz + g, t);
+    p = kg * h.w; t.hi = p; t.lo = fmaf(kg, h.w, -p) + kg * l.w; store_acc(G + 2 * nnz + g, t);
+  }
+};
+template <>
+struct AccSmem<NSI_FP64> {
+  T2<double>* __restrict__ a0;  // A, sum c_i x
+  T2<double>* __restrict__ a1;  // sum c_i y, sum c_i z
+  __device__ __forceinline__ AccSmem(unsigned char* p, size_t N)
+      : a0(reinterpret_cast<T2<double>*>(p)), a1(reinterpret_cast<T2<double>*>(p) + N) {}
+  __device__ __forceinline__ void zero(int k) {
+    a0[k] = {0.0, 0.0};
+    a1[k] = {0.0, 0.0};
+  }
+  __device__ __forceinline__ void add3(int k1, int k2, int k3, double A1, double A2, double A3, double gx,
+                                       double gy, double gz) {
+    T2<double> x1 = a0[k1], x2 = a0[k2], x3 = a0[k3];
+    T2<double> y1 = a1[k1], y2 = a1[k2], y3 = a1[k3];
+    x1.x += A1; x1.y += gx; y1.x += gy; y1.y += gz;
+    x2.x += A2; x2.y += gx; y2.x += gy; y2.y += gz;
+    x3.x += A3; x3.y += gx; y3.x += gy; y3.y += gz;
+    a0[k1] = x1; a0[k2] = x2; a0[k3] = x3;
+    a1[k1] = y1; a1[k2] = y2; a1[k3] = y3;
+  }
+  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_FP64>* r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      if (k == kd) continue;
+      const T2<double> x = a0[k], y = a1[k];
+      r[0].add(x.x); r[1].add(x.y); r[2].add(y.x); r[3].add(y.y);
+    }
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_FP64>* r) {
+    a0[k] = {r[0].v, r[1].v};
+    a1[k] = {r[2].v, r[3].v};
+  }
+  __device__ __forceinline__ void write(int k, double kg, double* A, double* G, int64_t nnz, int64_t g) const {
+    const T2<double> x = a0[k], y = a1[k];
+    A[g] = x.x;
+    G[g] = kg * x.y;
+    G[nnz + g] = kg * y.x;
+    G[2 * nnz + g] = kg * y.y;
+  }
+};
+
+// where the staging copies of a slot land before the edge vectors are formed:
+// the low coordinate part (mixed modes) and u_x, inside the accumulator
+// region (overwritten by the zeroing that follows) or in rawux
+template <int P>
+__device__ __forceinline__ float4* staged_lo(unsigned char* smem, const GatherSmem& lay, int k) {
+  return reinterpret_cast<float4*>(smem + lay.acc()) + k;
+}
+template <int P>
+__device__ __forceinline__ typename Prec<P>::T* staged_ux(unsigned char* smem, const GatherSmem& lay, int k) {
+  if constexpr (P == NSI_MIXED_F32_ACC32) return reinterpret_cast<float*>(smem + lay.rawux()) + k;
+  else if constexpr (P == NSI_MIXED_F32_ACC64) return reinterpret_cast<float*>(reinterpret_cast<float4*>(smem + lay.acc()) + lay.N() + k);
+  else return reinterpret_cast<double*>(reinterpret_cast<T2<double>*>(smem + lay.acc()) + k);
+}
+
+// reciprocal of det: the float path uses the fast approximate division
+// (about 1 ulp), the double path IEEE division
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+
+// Contribution of one element of row i's star, with node i as the origin.
+// With w = rho/120 (S + u_i) + mu/(6 det) c_i, the convection + viscous part
+// of A_e[i][j] is w . c_j (nsi_internal.cuh); the pressure-gradient part of
+// every entry of the row is -c_i / 24 (scaled at write-out); the element's
+// lumped mass is rho det / (24 dt) (det summed, scaled at the end).
+template <typename T>
+struct StarContrib {
+  int k1, k2, k3;  // slots of the three other nodes
+  T A1, A2, A3;
+  V3<T> ci;
+  T det;
+};
+
+template <typename T>
+__device__ __forceinline__ StarContrib<T> star_contrib(unsigned w, const T4<T>* __restrict__ nb0,
+                                                       const T2<T>* __restrict__ nb1, int t, int R,
+                                                       const V3<T>& u2i, T kc, T kmu) {
+  StarContrib<T> r;
+  r.k1 = (int)(w & 31) * R + t;
+  r.k2 = (int)((w >> 5) & 31) * R + t;
+  r.k3 = (int)((w >> 10) & 31) * R + t;
+  const T4<T> a1 = nb0[r.k1], a2 = nb0[r.k2], a3 = nb0[r.k3];
+  const T2<T> b1 = nb1[r.k1], b2 = nb1[r.k2], b3 = nb1[r.k3];
+  const V3<T> d1{a1.x, a1.y, a1.z}, d2{a2.x, a2.y, a2.z}, d3{a3.x, a3.y, a3.z};
+  // Jacobian cofactors (calculate_cartesian_derivatives) with i as the origin
+  const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
+  r.det = dot(d1, c1);
+  r.ci = {-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
+  const T kv = kmu * rcp_fast(r.det);
+  // w = rho/120 (2 u_i + u_1 + u_2 + u_3) + mu/(6 det) c_i
+  const V3<T> w3{kc * (u2i.x + a1.w + a2.w + a3.w) + kv * r.ci.x, kc * (u2i.y + b1.x + b2.x + b3.x) + kv * r.ci.y,
+                 kc * (u2i.z + b1.y + b2.y + b3.y) + kv * r.ci.z};
+  r.A1 = dot(w3, c1);
+  r.A2 = dot(w3, c2);
+  r.A3 = dot(w3, c3);
+  return r;
+}
+
+template <int P, bool DEBUG>
+__device__ __forceinline__ bool star_ok(unsigned w, int len) {
+  return !DEBUG || ((int)(w & 31) < len && (int)((w >> 5) & 31) < len && (int)((w >> 10) & 31) < len);
+}
+
+// the element loop of one row: 4 elements computed before their accumulation
+template <int P, bool DEBUG>
+__device__ __forceinline__ void star_loop(const uint16_t* __restrict__ star, int s0, int s1, int len,
+                                          const T4<typename Prec<P>::T>* __restrict__ nb0,
+                                          const T2<typename Prec<P>::T>* __restrict__ nb1, AccSmem<P>& acc, int t,
+                                          int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
+                                          typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
+  using T = typename Prec<P>::T;
+  int s = s0;
+  for (; s + 3 < s1; s += 4) {
+    const unsigned w0 = star[s], w1 = star[s + 1], w2 = star[s + 2], w3 = star[s + 3];
+    if (DEBUG && !(star_ok<P, DEBUG>(w0, len) && star_ok<P, DEBUG>(w1, len) && star_ok<P, DEBUG>(w2, len) &&
+                   star_ok<P, DEBUG>(w3, len))) {
+      atomicOr(err, ERR_STAR);
+      continue;
+    }
+    const StarContrib<T> a = star_contrib<T>(w0, nb0, nb1, t, R, u2i, kc, kmu);
+    const StarContrib<T> b = star_contrib<T>(w1, nb0, nb1, t, R, u2i, kc, kmu);
+    const StarContrib<T> c = star_contrib<T>(w2, nb0, nb1, t, R, u2i, kc, kmu);
+    const StarContrib<T> d = star_contrib<T>(w3, nb0, nb1, t, R, u2i, kc, kmu);
+    acc.add3(a.k1, a.k2, a.k3, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
+    acc.add3(b.k1, b.k2, b.k3, b.A1, b.A2, b.A3, b.ci.x, b.ci.y, b.ci.z);
+    acc.add3(c.k1, c.k2, c.k3, c.A1, c.A2, c.A3, c.ci.x, c.ci.y, c.ci.z);
+    acc.add3(d.k1, d.k2, d.k3, d.A1, d.A2, d.A3, d.ci.x, d.ci.y, d.ci.z);
+    detsum.add(a.det);
+    detsum.add(b.det);
+    detsum.add(c.det);
+    detsum.add(d.det);
+  }
+  for (; s < s1; ++s) {
+    const unsigned w0 = star[s];
+    if (!star_ok<P, DEBUG>(w0, len)) {
+      atomicOr(err, ERR_STAR);
+      continue;
+    }
+    const StarContrib<T> a = star_contrib<T>(w0, nb0, nb1, t, R, u2i, kc, kmu);
+    acc.add3(a.k1, a.k2, a.k3, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
+    detsum.add(a.det);
+  }
 }
 
 // one block of rows [r0, r0 + blockDim.x) of one mesh
 template <int P, bool DEBUG>
 __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& f, const OutView& o, int64_t r0,
-                                            Entry<P>* __restrict__ ent) {
+                                            unsigned char* smem, const GatherSmem& lay) {
   using T = typename Prec<P>::T;
   using Out = typename Prec<P>::Out;
   const int R = blockDim.x;
+  const int t = threadIdx.x;
   const int64_t r_end = min(r0 + (int64_t)R, m.n);
-  const int64_t i = r0 + threadIdx.x;
-  const int32_t base = m.row_ptr[r0];
-  const int32_t bend = m.row_ptr[r_end];
+  const int nrows = (int)(r_end - r0);
+  const int32_t base = m.row_ptr[r0], bend = m.row_ptr[r_end];
+  const int L = bend - base;
+  const int32_t sbase = m.star_ptr[r0], send = m.star_ptr[r_end];
+  const int S = send - sbase;
+  if (DEBUG && (L > lay.L || S > lay.S || R != lay.R)) {
+    if (t == 0) atomicOr(m.err, ERR_STAR);
+    return;
+  }
+  T4<T>* __restrict__ nb0 = reinterpret_cast<T4<T>*>(smem + lay.nb0());
+  T2<T>* __restrict__ nb1 = reinterpret_cast<T2<T>*>(smem + lay.nb1());
+  AccSmem<P> acc(smem + lay.acc(), lay.N());
+  int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
+  uint8_t* erow = smem + lay.erow();
+  int32_t* lbs = reinterpret_cast<int32_t*>(smem + lay.lb());
+  uint16_t* star = reinterpret_cast<uint16_t*>(smem + lay.star());
   const T kc = (T)(f.rho / 120.0);
   const T kmu = (T)(f.mu / 6.0);
   const T kmass = (T)(f.rho / (24.0 * f.dt));
   const T kg = (T)(-1.0 / 24.0);
-  Out* A = static_cast<Out*>(o.A);
-  Out* G = static_cast<Out*>(o.G);
-  Out* Rh = static_cast<Out*>(o.rhs);
 
-  if (i < r_end) {
-    const int32_t rs = m.row_ptr[i], re = m.row_ptr[i + 1];
-    const int len = re - rs;
-    Entry<P>* row = ent + (rs - base);
-    NodeX<P> xi;
+  // phase 0: the row's scalars, the entry -> row map; the block's column
+  // indices and row-gather words (coalesced)
+  const int64_t i = r0 + t;
+  int32_t rs = 0, re = 0, s0 = 0, s1 = 0;
+  int dp = 0;
+  V3<T> uni{T(0), T(0), T(0)};
+  NodeX<P> xi;
+  if (t < nrows) {
+    rs = m.row_ptr[i];
+    re = m.row_ptr[i + 1];
+    s0 = m.star_ptr[i] - sbase;
+    s1 = m.star_ptr[i + 1] - sbase;
+    dp = m.diag_pos[i];
+    uni = load_vec<T>(f.un, i);
     xi.load(m, i);
-    const V3<T> ui = load_vec<T>(f.u, i);
-    // stage the row's neighbours (calculate_transients for every element of the star)
-    for (int q = 0; q < len; ++q) {
-      const int j = m.col_idx[rs + q];
+    lbs[t] = rs - base;
+    for (int k = rs - base; k < re - base; ++k) erow[k] = (uint8_t)t;
+  }
+  for (int k = t; k < L; k += R) col[k] = m.col_idx[base + k];
+  for (int k = t; k < S; k += R) star[k] = m.star[sbase + k];
+  __syncthreads();
+
+  const int len = re - rs;
+  const int lb = rs - base;
+  Acc<P> detsum;
+  detsum.zero();
+  if (t < nrows) {
+    // phase 1 (calculate_transients for the row): gather every neighbour's
+    // coordinates and velocity with asynchronous copies, all in flight at once
+    const T* u0 = static_cast<const T*>(f.u[0]);
+    const T* u1 = static_cast<const T*>(f.u[1]);
+    const T* u2 = static_cast<const T*>(f.u[2]);
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      const int j = col[lb + q];
       if (DEBUG && (j < 0 || j >= m.n)) {
         atomicOr(m.err, ERR_BAD_INDEX);
         continue;
       }
-      NodeX<P> xj;
-      xj.load(m, j);
-      row[q].d = xj.minus(xi);
-      row[q].u = load_vec<T>(f.u, j);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) row[q].a[c].zero();
-    }
-    // every element containing node i, with i as the local origin
-    Acc<P> adiag, gdx, gdy, gdz, mass;
-    adiag.zero();
-    gdx.zero();
-    gdy.zero();
-    gdz.zero();
-    mass.zero();
-    const int32_t ss = m.star_ptr[i], se = m.star_ptr[i + 1];
-    for (int32_t s = ss; s < se; ++s) {
-      const unsigned w = m.star[s];
-      const int p1 = w & 31, p2 = (w >> 5) & 31, p3 = (w >> 10) & 31;
-      if (DEBUG && (p1 >= len || p2 >= len || p3 >= len)) {
-        atomicOr(m.err, ERR_STAR);
-        continue;
+      if constexpr (P == NSI_FP64) {
+        cp_async16(&nb0[k], &m.xyz64[j]);
+        cp_async16(reinterpret_cast<char*>(&nb0[k]) + 16, reinterpret_cast<const char*>(&m.xyz64[j]) + 16);
+      } else {
+        cp_async16(&nb0[k], &m.xyz_hi[j]);
+        cp_async16(staged_lo<P>(smem, lay, k), &m.xyz_lo[j]);
       }
-      const V3<T> d1 = row[p1].d, d2 = row[p2].d, d3 = row[p3].d;
-      const V3<T> u1 = row[p1].u, u2 = row[p2].u, u3 = row[p3].u;
-      const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
-      const T det = dot(d1, c1);
-      const V3<T> ci = {-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
-      const V3<T> v = add(add(add(ui, ui), add(u1, u2)), u3);  // S + u_i
-      const T kv = kmu * rcp(det);
-      const V3<T> g = {kg * ci.x, kg * ci.y, kg * ci.z};
-      row[p1].a[0].add(kc * dot(v, c1) + kv * dot(ci, c1));
-      row[p2].a[0].add(kc * dot(v, c2) + kv * dot(ci, c2));
-      row[p3].a[0].add(kc * dot(v, c3) + kv * dot(ci, c3));
-      row[p1].a[1].add(g.x);
-      row[p1].a[2].add(g.y);
-      row[p1].a[3].add(g.z);
-      row[p2].a[1].add(g.x);
-      row[p2].a[2].add(g.y);
-      row[p2].a[3].add(g.z);
-      row[p3].a[1].add(g.x);
-      row[p3].a[2].add(g.y);
-      row[p3].a[3].add(g.z);
-      const T km = kmass * det;
-      adiag.add(kc * dot(v, ci) + kv * dot(ci, ci) + km);
-      gdx.add(g.x);
-      gdy.add(g.y);
-      gdz.add(g.z);
-      mass.add(km);
+      cp_async_t(staged_ux<P>(smem, lay, k), u0 + j);
+      cp_async_t(&nb1[k].x, u1 + j);
+      cp_async_t(&nb1[k].y, u2 + j);
     }
-    // diagonal entry of the row
-    const int dp = m.diag_pos[i];
-    if (len == 0) {
-      // node in no element: empty row, zero right-hand side
-    } else if (!DEBUG || dp < len) {
-      row[dp].a[0] = adiag;
-      row[dp].a[1] = gdx;
-      row[dp].a[2] = gdy;
-      row[dp].a[3] = gdz;
-    } else {
-      atomicOr(m.err, ERR_STAR);
+    cp_async_wait_all();
+    // edge vectors d = x_j - x_i (float: (hi_j - hi_i) + (lo_j - lo_i)); the
+    // slots are this thread's own, so no barrier is needed
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      const T4<T> h = nb0[k];
+      V3<T> d;
+      if constexpr (P == NSI_FP64) {
+        d = sub(V3<T>{h.x, h.y, h.z}, xi.x);
+      } else {
+        const float4 l = *staged_lo<P>(smem, lay, k);
+        d = add(sub(V3<T>{h.x, h.y, h.z}, xi.hi), sub(V3<T>{l.x, l.y, l.z}, xi.lo));
+      }
+      const T ux = *staged_ux<P>(smem, lay, k);
+      nb0[k] = T4<T>{d.x, d.y, d.z, ux};
+      acc.zero(k);
+    }
+    // phase 2: every element of the row's star, accumulated privately
+    if (len > 0) {
+      if (DEBUG && dp >= len) atomicOr(m.err, ERR_STAR);
+      const int kd = dp * R + t;
+      const T4<T> di = nb0[kd];
+      const T2<T> ei = nb1[kd];
+      const V3<T> u2i{di.w + di.w, ei.x + ei.x, ei.y + ei.y};
+      star_loop<P, DEBUG>(star, s0, s1, len, nb0, nb1, acc, t, R, u2i, kc, kmu, detsum, m.err);
+      // diagonal from the partition of unity (sum_b grad N_b = 0, exact):
+      //   A(i,i) = lumped mass - sum_{j != i} A(i,j)   (convection + viscous parts)
+      //   G(i,i) = 1/3 sum_{j != i} G(i,j)            (each element adds c_i to three
+      //                                                 off-diagonal entries and the diagonal)
+      Acc<P> rsum[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rsum[c].zero();
+      acc.row_sums(t, R, len, kd, rsum);
+      Acc<P> dg[4];
+      if constexpr (P == NSI_MIXED_F32_ACC64) {
+        const float p = kmass * detsum.hi;  // kmass * (hi + lo), product error kept
+        dg[0].hi = p;
+        dg[0].lo = fmaf(kmass, detsum.hi, -p) + kmass * detsum.lo;
+        dg[0].add(-rsum[0].hi);
+        dg[0].lo -= rsum[0].lo;
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+          const float q = rsum[c].hi * (1.0f / 3.0f);
+          dg[c].hi = q;
+          dg[c].lo = fmaf(rsum[c].hi, 1.0f / 3.0f, -q) + rsum[c].lo * (1.0f / 3.0f);
+        }
+      } else {
+        dg[0].v = kmass * detsum.v - rsum[0].v;
+#pragma unroll
+        for (int c = 1; c < 4; ++c) dg[c].v = rsum[c].v * (T(1) / T(3));
+      }
+      if (!DEBUG || dp < len) acc.set(kd, dg);
     }
     // lumped RHS: (sum_e rho |T_e| / (4 dt)) u^n_i
-    const V3<T> uni = load_vec<T>(f.un, i);
     const T unk[3] = {uni.x, uni.y, uni.z};
+    Out* Rh = static_cast<Out*>(o.rhs);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       Acc<P> r;
+      const T c = kmass * unk[k];
       if constexpr (P == NSI_MIXED_F32_ACC64) {
-        // (hi + lo) * u, keeping the product error (FMA-based TwoProd)
-        float p = mass.hi * unk[k];
-        float e = fmaf(mass.hi, unk[k], -p) + mass.lo * unk[k];
+        const float p = detsum.hi * c;
         r.hi = p;
-        r.lo = e;
+        r.lo = fmaf(detsum.hi, c, -p) + detsum.lo * c;
       } else {
-        r.v = mass.v * unk[k];
+        r.v = detsum.v * c;
       }
       store_acc(Rh + k * m.n + i, r);
     }
   }
   __syncthreads();
-  // coalesced write of the block's contiguous slice of A and G
-  for (int32_t t = threadIdx.x; t < bend - base; t += R) {
-    const Entry<P>& en = ent[t];
-    store_acc(A + base + t, en.a[0]);
-    store_acc(G + base + t, en.a[1]);
-    store_acc(G + m.nnz + base + t, en.a[2]);
-    store_acc(G + 2 * m.nnz + base + t, en.a[3]);
+  // phase 3: coalesced write of the block's contiguous slice of A and G
+  Out* A = static_cast<Out*>(o.A);
+  Out* G = static_cast<Out*>(o.G);
+  for (int k = t; k < L; k += R) {
+    const int r = erow[k];
+    acc.write((k - lbs[r]) * R + r, kg, A, G, m.nnz, (int64_t)base + k);
   }
 }
 
 template <int P, bool DEBUG>
-__global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, OutView o) {
+__global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, OutView o, GatherSmem lay) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  gather_rows<P, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, reinterpret_cast<Entry<P>*>(smem_raw));
+  gather_rows<P, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, smem_raw, lay);
 }
 
 // ------------------------------------------------------ batched kernel ---
@@ -422,7 +718,7 @@ struct BatchArgs {
 };
 
 template <int P>
-__global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ BatchArgs args, GatherSmem lay) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int64_t b = blockIdx.x; b < args.total_blocks; b += gridDim.x) {
     // mesh of global block b: last item with block0 <= b
@@ -433,7 +729,7 @@ __global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ Ba
       else hi = mid - 1;
     }
     const BatchItem& it = args.item[lo];
-    gather_rows<P, false>(it.m, it.f, it.o, (b - it.block0) * blockDim.x, reinterpret_cast<Entry<P>*>(smem_raw));
+    gather_rows<P, false>(it.m, it.f, it.o, (b - it.block0) * blockDim.x, smem_raw, lay);
     __syncthreads();  // the next block reuses the shared records
   }
 }
@@ -637,10 +933,11 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
   nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
   if (st) return st;
-  const size_t smem = (size_t)h->plan.max_block_entries * sizeof(Entry<P>);
   const int R = h->plan.rows_per_block;
-  if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o);
-  else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o);
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
+  const size_t smem = lay.total();
+  if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
+  else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
   return check_launch("gather_kernel");
 }
 
@@ -684,31 +981,36 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   args.count = count;
+  // one block size for the whole batch: the smallest planned one.  A mesh's
+  // per-block maxima, taken over blocks of its own (larger or equal) size,
+  // bound its blocks of the smaller size too.
+  int R = 1 << 30, max_entries = 0, max_stars = 0, max_row = 1;
+  for (int k = 0; k < count; ++k) R = std::min(R, hs[k]->plan.rows_per_block);
   int64_t blocks = 0;
-  int R = 0, max_entries = 0;
   for (int k = 0; k < count; ++k) {
     const NsiHandle* h = hs[k];
-    if (R == 0) R = h->plan.rows_per_block;
-    if (h->plan.rows_per_block != R)
-      return fail(NSI_ERR_UNSUPPORTED, "batched meshes must share one rows-per-block plan");
     max_entries = std::max(max_entries, h->plan.max_block_entries);
+    max_stars = std::max(max_stars, h->plan.max_block_stars);
+    max_row = std::max(max_row, h->max_row);
     args.item[k].m = view_of(h);
     args.item[k].f = fields_of(&fs[k]);
     args.item[k].o = OutView{os[k].A_val, os[k].G_val, os[k].rhs};
     args.item[k].block0 = blocks;
-    blocks += h->plan.n_blocks;
+    blocks += (h->n + R - 1) / R;
   }
   args.total_blocks = blocks;
   if (blocks == 0) return NSI_OK;
   nsi_status st = set_gather_smem<P, false>();
   if (st) return st;
-  const size_t smem = (size_t)max_entries * sizeof(Entry<P>);
+  const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_stars);
+  const size_t smem = lay.total();
+  if (smem > 200 * 1024) return fail(NSI_ERR_UNSUPPORTED, "batched meshes need more shared memory than a block has");
   int per_sm = 0, sms = 0, dev = 0;
   NSI_CUDA(cudaGetDevice(&dev));
   NSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   NSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<P>, R, smem));
   const int64_t grid = std::min<int64_t>(blocks, (int64_t)std::max(1, per_sm) * sms);
-  batched_kernel<P><<<grid, R, smem, s>>>(args);
+  batched_kernel<P><<<grid, R, smem, s>>>(args, lay);
   return check_launch("batched_kernel");
 }
 
@@ -732,6 +1034,15 @@ static nsi_status residual_p(NsiHandle* h, const FieldView& f, void* r, cudaStre
   const int blk = 256;
   residual_kernel<P><<<(h->E + blk - 1) / blk, blk, 0, s>>>(view_of(h), f, r);
   return check_launch("residual_kernel");
+}
+
+int gather_kernel_regs(int precision) {
+  cudaFuncAttributes a{};
+  cudaError_t e;
+  if (precision == NSI_FP64) e = cudaFuncGetAttributes(&a, gather_kernel<NSI_FP64, false>);
+  else if (precision == NSI_MIXED_F32_ACC64) e = cudaFuncGetAttributes(&a, gather_kernel<NSI_MIXED_F32_ACC64, false>);
+  else e = cudaFuncGetAttributes(&a, gather_kernel<NSI_MIXED_F32_ACC32, false>);
+  return e == cudaSuccess ? a.numRegs : 96;
 }
 
 }  // namespace nsi

@@ -167,7 +167,7 @@ def test_residual_matches_oracle(precision):
     uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
     uno = un if precision == "fp64" else un.astype(np.float32).astype(np.float64)
     rp, ci, oA, oG, orhs = oracle.assemble(mesh.coord, mesh.lnods, uo, uno)
-    Ro = oracle.residual((rp, ci, oA), orhs.T, uo)   # [n, 3]
+    Ro = oracle.residual((rp, ci, oA), orhs, uo)   # [n, 3]
     tol = 1e-12 if precision == "fp64" else 1e-5
     scale = np.abs(Ro).max()
     assert np.abs(R.T - Ro).max() <= tol * scale * 10
