@@ -70,6 +70,7 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->xyz_hi);
   cudaFree(h->xyz_lo);
   cudaFree(h->err);
+  cudaFree(h->rec);
   cudaFree(h->stage);
   delete h;
 }
@@ -299,6 +300,11 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   } else {
     if ((st = dev_upload(h, &h->xyz_hi, xhi.data(), n, s))) return st;
     if ((st = dev_upload(h, &h->xyz_lo, xlo.data(), n, s))) return st;
+  }
+  if (h->gather_ok) {
+    h->rec_bytes = h->precision == NSI_FP64 ? 64 : 32;
+    NSI_CUDA(cudaMalloc(&h->rec, (size_t)h->rec_bytes * n));
+    h->device_bytes += (int64_t)h->rec_bytes * n;
   }
   NSI_CUDA(cudaMalloc((void**)&h->err, sizeof(unsigned)));
   NSI_CUDA(cudaMemsetAsync(h->err, 0, sizeof(unsigned), s));

@@ -56,10 +56,9 @@ struct GatherPlan {
 //   nb0   T[4] per slot: edge vector d = x_j - x_i and u_x of the neighbour
 //   nb1   T[2] per slot: u_y, u_z
 //   acc   accumulators per slot (ab bytes): A and the three sums of c_i
-//   rawux float per slot (single-accumulator float mode only; the other
-//         modes stage u_x inside acc)
 //   col   int32 per CSR entry, erow uint8 per CSR entry (its row), lb int32
-//         per row (row start inside the block's CSR range), star uint16 per word
+//         per row (row start inside the block's CSR range), star uint16 per
+//         word (copied as aligned pairs, so S + 2 of them)
 // Used identically by the host (launch size) and the kernel (carving).
 struct GatherSmem {
   int R, W, L, S, tb, ab;
@@ -68,12 +67,11 @@ struct GatherSmem {
   __host__ __device__ size_t nb0() const { return 0; }
   __host__ __device__ size_t nb1() const { return up16(nb0() + (size_t)4 * tb * N()); }
   __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
-  __host__ __device__ size_t rawux() const { return up16(acc() + (size_t)ab * N()); }
-  __host__ __device__ size_t col() const { return up16(rawux() + (ab == 16 ? (size_t)4 * N() : 0)); }
+  __host__ __device__ size_t col() const { return up16(acc() + (size_t)ab * N()); }
   __host__ __device__ size_t erow() const { return up16(col() + (size_t)4 * L); }
   __host__ __device__ size_t lb() const { return up16(erow() + (size_t)L); }
   __host__ __device__ size_t star() const { return up16(lb() + (size_t)4 * R); }
-  __host__ __device__ size_t total() const { return up16(star() + (size_t)2 * S); }
+  __host__ __device__ size_t total() const { return up16(star() + (size_t)2 * (S + 2)); }
 };
 
 __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S) {
@@ -119,6 +117,11 @@ struct NsiHandle {
   nsi::D4* xyz64 = nullptr;
   float4* xyz_hi = nullptr;
   float4* xyz_lo = nullptr;
+  // per-call node records for the row-gather kernel (one 32-byte record per node
+  // in the mixed modes, 64 bytes in FP64): coordinates and velocity of a node
+  // in one or two DRAM sectors, rebuilt at the start of every gather call
+  void* rec = nullptr;
+  int rec_bytes = 0;
   // device error word
   unsigned* err = nullptr;
   // staging for nsi_assemble_host (allocated on first use)
@@ -191,24 +194,19 @@ __device__ __forceinline__ long long f32_to_f64_bits(float f) {
 
 // double nearest to hi + lo for a compensated pair with |lo| <= ulp_float(hi)
 // (the result of TwoSum accumulation): the double bits of hi plus lo expressed
-// in units of hi's double ulp (2^(e_hi - 179) for a normal float hi), rounded
-// to nearest (one double ulp at most).  Finite inputs only.
+// in units of hi's double ulp, rounded to nearest (one double ulp at most).
+// A normal float hi with biased exponent e has double ulp 2^(e - 179); lo is
+// scaled by the exact power of two 2^(179 - e).  Finite inputs only.
 __device__ __forceinline__ long long pair_to_f64_bits(float hi, float lo) {
-  if (hi == 0.0f) return f32_to_f64_bits(lo);
-  long long bits = f32_to_f64_bits(hi);
-  unsigned uh = __float_as_uint(hi);
-  unsigned eh = (uh >> 23) & 0xffu;
-  unsigned ul = __float_as_uint(lo);
-  unsigned el = (ul >> 23) & 0xffu;
-  if (el == 0u || eh == 0u) return bits;  // lo zero/subnormal, or hi subnormal: lo below resolution
-  // scale lo by 2^(179 - eh) through its exponent field: el' = el + 179 - eh
-  int el2 = (int)el + 179 - (int)eh;
-  if (el2 <= 0) return bits;                      // below half an ulp
-  if (el2 >= 127 + 30) return bits;               // not a normalised pair; ignore
-  float scaled = __uint_as_float((ul & 0x807fffffu) | ((unsigned)el2 << 23));
-  int k = __float2int_rn(scaled);
+  const unsigned uh = __float_as_uint(hi);
+  const unsigned eh = (uh >> 23) & 0xffu;
+  if (eh < 52u) return f32_to_f64_bits(hi + lo);  // zero, subnormal or |hi| < 2^-75: the float sum
+  const unsigned hi32 = (uh & 0x80000000u) | ((eh + 896u) << 20) | ((uh & 0x7fffffu) >> 3);
+  const long long bits = (long long)(((unsigned long long)hi32 << 32) | (uh << 29));
+  int k = __float2int_rn(lo * __uint_as_float((306u - eh) << 23));
   // hi an exact power of two and lo of opposite sign: the sum lies in the binade
   // below, whose ulp is half as large
+  const unsigned ul = __float_as_uint(lo);
   if ((uh & 0x7fffffu) == 0u && ((uh ^ ul) & 0x80000000u)) k *= 2;
   // hi's sign decides the direction of the integer step on the magnitude bits
   return (uh & 0x80000000u) ? bits - (long long)k : bits + (long long)k;

@@ -32,6 +32,7 @@ struct MeshView {
   const D4* __restrict__ xyz64;
   const float4* __restrict__ xyz_hi;
   const float4* __restrict__ xyz_lo;
+  const void* __restrict__ rec;
   unsigned* err;
 };
 
@@ -61,6 +62,7 @@ static MeshView view_of(const NsiHandle* h) {
   m.xyz64 = h->xyz64;
   m.xyz_hi = h->xyz_hi;
   m.xyz_lo = h->xyz_lo;
+  m.rec = h->rec;
   m.err = h->err;
   return m;
 }
@@ -158,6 +160,40 @@ template <typename T>
 __device__ __forceinline__ void cp_async_t(T* dst, const T* src) {
   if constexpr (sizeof(T) == 8) cp_async8(dst, src);
   else cp_async4(dst, src);
+}
+
+// ---------------------------------------------------------- node records ---
+// One record per node, rebuilt every call from the handle's coordinates and
+// the caller's velocities, so that the row-gather kernel fetches a neighbour
+// with one 32-byte (mixed) or 64-byte (FP64) request instead of five:
+//   mixed: {hx, hy, hz, ux} {uy, uz, lo_xy, lo_z}, lo_* the top 16 bits of
+//          the float low parts (coordinates kept to ~2^-32 relative)
+//   FP64:  {x, y, z, 0} {ux, uy, uz, 0} as doubles
+template <int P>
+__global__ void __launch_bounds__(256) pack_kernel(MeshView m, FieldView f, void* __restrict__ rec) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m.n) return;
+  if constexpr (P == NSI_FP64) {
+    const D4 x = m.xyz64[i];
+    const V3<double> u = load_vec<double>(f.u, i);
+    D4* r = static_cast<D4*>(rec) + 2 * i;
+    r[0] = D4{x.x, x.y, x.z, 0.0};
+    r[1] = D4{u.x, u.y, u.z, 0.0};
+  } else {
+    const float4 hi = __ldg(m.xyz_hi + i);
+    const float4 lo = __ldg(m.xyz_lo + i);
+    const V3<float> u = load_vec<float>(f.u, i);
+    uint4* r = static_cast<uint4*>(rec) + 2 * i;
+    r[0] = make_uint4(__float_as_uint(hi.x), __float_as_uint(hi.y), __float_as_uint(hi.z), __float_as_uint(u.x));
+    r[1] = make_uint4(__float_as_uint(u.y), __float_as_uint(u.z),
+                      (__float_as_uint(lo.x) >> 16) | (__float_as_uint(lo.y) & 0xffff0000u),
+                      __float_as_uint(lo.z) & 0xffff0000u);
+  }
+}
+
+__device__ __forceinline__ V3<float> record_lo(float w6, float w7) {
+  const unsigned a = __float_as_uint(w6), b = __float_as_uint(w7);
+  return {__uint_as_float(a << 16), __uint_as_float(a & 0xffff0000u), __uint_as_float(b & 0xffff0000u)};
 }
 
 // ------------------------------------------------ element-centric kernel ---
@@ -437,18 +473,12 @@ struct AccSmem<NSI_FP64> {
   }
 };
 
-// where the staging copies of a slot land before the edge vectors are formed:
-// the low coordinate part (mixed modes) and u_x, inside the accumulator
-// region (overwritten by the zeroing that follows) or in rawux
+// where the second half of a neighbour's record lands before the edge vectors
+// are formed: inside the slot's accumulators, which are zeroed right after
 template <int P>
-__device__ __forceinline__ float4* staged_lo(unsigned char* smem, const GatherSmem& lay, int k) {
-  return reinterpret_cast<float4*>(smem + lay.acc()) + k;
-}
-template <int P>
-__device__ __forceinline__ typename Prec<P>::T* staged_ux(unsigned char* smem, const GatherSmem& lay, int k) {
-  if constexpr (P == NSI_MIXED_F32_ACC32) return reinterpret_cast<float*>(smem + lay.rawux()) + k;
-  else if constexpr (P == NSI_MIXED_F32_ACC64) return reinterpret_cast<float*>(reinterpret_cast<float4*>(smem + lay.acc()) + lay.N() + k);
-  else return reinterpret_cast<double*>(reinterpret_cast<T2<double>*>(smem + lay.acc()) + k);
+__device__ __forceinline__ void* staged_half(unsigned char* smem, const GatherSmem& lay, int k, int part) {
+  if constexpr (P == NSI_FP64) return reinterpret_cast<T2<double>*>(smem + lay.acc()) + (size_t)part * lay.N() + k;
+  else return reinterpret_cast<float4*>(smem + lay.acc()) + k;
 }
 
 // reciprocal of det: the float path uses the fast approximate division
@@ -570,26 +600,30 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   const T kmass = (T)(f.rho / (24.0 * f.dt));
   const T kg = (T)(-1.0 / 24.0);
 
-  // phase 0: the row's scalars, the entry -> row map; the block's column
-  // indices and row-gather words (coalesced)
+  // phase 0: the row's scalars and the entry -> row map; the block's column
+  // indices and row-gather words by asynchronous copies (all in flight)
   const int64_t i = r0 + t;
   int32_t rs = 0, re = 0, s0 = 0, s1 = 0;
   int dp = 0;
   V3<T> uni{T(0), T(0), T(0)};
-  NodeX<P> xi;
+  const int soff = sbase & 1;  // star words are copied as aligned pairs
   if (t < nrows) {
     rs = m.row_ptr[i];
     re = m.row_ptr[i + 1];
-    s0 = m.star_ptr[i] - sbase;
-    s1 = m.star_ptr[i + 1] - sbase;
+    s0 = m.star_ptr[i] - sbase + soff;
+    s1 = m.star_ptr[i + 1] - sbase + soff;
     dp = m.diag_pos[i];
     uni = load_vec<T>(f.un, i);
-    xi.load(m, i);
     lbs[t] = rs - base;
     for (int k = rs - base; k < re - base; ++k) erow[k] = (uint8_t)t;
   }
-  for (int k = t; k < L; k += R) col[k] = m.col_idx[base + k];
-  for (int k = t; k < S; k += R) star[k] = m.star[sbase + k];
+  for (int k = t; k < L; k += R) cp_async4(&col[k], m.col_idx + base + k);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(m.star + (sbase - soff));
+    const int words = (S + soff + 1) >> 1;
+    for (int k = t; k < words; k += R) cp_async4(reinterpret_cast<uint32_t*>(star) + k, src + k);
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   const int len = re - rs;
@@ -597,43 +631,57 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   Acc<P> detsum;
   detsum.zero();
   if (t < nrows) {
-    // phase 1 (calculate_transients for the row): gather every neighbour's
-    // coordinates and velocity with asynchronous copies, all in flight at once
-    const T* u0 = static_cast<const T*>(f.u[0]);
-    const T* u1 = static_cast<const T*>(f.u[1]);
-    const T* u2 = static_cast<const T*>(f.u[2]);
+    // phase 1 (calculate_transients for the row): every neighbour's record,
+    // by asynchronous copies all in flight at once
+    const unsigned char* recs = static_cast<const unsigned char*>(m.rec);
+    constexpr int RB = P == NSI_FP64 ? 64 : 32;
     for (int q = 0, k = t; q < len; ++q, k += R) {
       const int j = col[lb + q];
       if (DEBUG && (j < 0 || j >= m.n)) {
         atomicOr(m.err, ERR_BAD_INDEX);
         continue;
       }
+      const unsigned char* r = recs + (size_t)j * RB;
       if constexpr (P == NSI_FP64) {
-        cp_async16(&nb0[k], &m.xyz64[j]);
-        cp_async16(reinterpret_cast<char*>(&nb0[k]) + 16, reinterpret_cast<const char*>(&m.xyz64[j]) + 16);
+        cp_async16(&nb0[k], r);
+        cp_async16(reinterpret_cast<char*>(&nb0[k]) + 16, r + 16);
+        cp_async16(staged_half<P>(smem, lay, k, 0), r + 32);
+        cp_async16(staged_half<P>(smem, lay, k, 1), r + 48);
       } else {
-        cp_async16(&nb0[k], &m.xyz_hi[j]);
-        cp_async16(staged_lo<P>(smem, lay, k), &m.xyz_lo[j]);
+        cp_async16(&nb0[k], r);
+        cp_async16(staged_half<P>(smem, lay, k, 0), r + 16);
       }
-      cp_async_t(staged_ux<P>(smem, lay, k), u0 + j);
-      cp_async_t(&nb1[k].x, u1 + j);
-      cp_async_t(&nb1[k].y, u2 + j);
     }
     cp_async_wait_all();
-    // edge vectors d = x_j - x_i (float: (hi_j - hi_i) + (lo_j - lo_i)); the
-    // slots are this thread's own, so no barrier is needed
-    for (int q = 0, k = t; q < len; ++q, k += R) {
-      const T4<T> h = nb0[k];
-      V3<T> d;
+    // edge vectors d = x_j - x_i; the row's own record (its diagonal slot)
+    // gives the origin.  The slots are this thread's own: no barrier needed.
+    if (len > 0) {
+      const int kd = dp * R + t;
       if constexpr (P == NSI_FP64) {
-        d = sub(V3<T>{h.x, h.y, h.z}, xi.x);
+        const T4<T> hi = nb0[kd];
+        const V3<T> xi{hi.x, hi.y, hi.z};
+        for (int q = 0, k = t; q < len; ++q, k += R) {
+          const T4<T> h = nb0[k];
+          const T2<T> ua = *static_cast<T2<T>*>(staged_half<P>(smem, lay, k, 0));
+          const T2<T> ub = *static_cast<T2<T>*>(staged_half<P>(smem, lay, k, 1));
+          nb0[k] = T4<T>{h.x - xi.x, h.y - xi.y, h.z - xi.z, ua.x};
+          nb1[k] = T2<T>{ua.y, ub.x};
+          acc.zero(k);
+        }
       } else {
-        const float4 l = *staged_lo<P>(smem, lay, k);
-        d = add(sub(V3<T>{h.x, h.y, h.z}, xi.hi), sub(V3<T>{l.x, l.y, l.z}, xi.lo));
+        const T4<T> hi = nb0[kd];
+        const float4 si = *static_cast<float4*>(staged_half<P>(smem, lay, kd, 0));
+        const V3<float> xh{hi.x, hi.y, hi.z};
+        const V3<float> xl = record_lo(si.z, si.w);
+        for (int q = 0, k = t; q < len; ++q, k += R) {
+          const T4<T> h = nb0[k];
+          const float4 sv = *static_cast<float4*>(staged_half<P>(smem, lay, k, 0));
+          const V3<float> d = add(sub(V3<float>{h.x, h.y, h.z}, xh), sub(record_lo(sv.z, sv.w), xl));
+          nb0[k] = T4<T>{d.x, d.y, d.z, h.w};
+          nb1[k] = T2<T>{sv.x, sv.y};
+          acc.zero(k);
+        }
       }
-      const T ux = *staged_ux<P>(smem, lay, k);
-      nb0[k] = T4<T>{d.x, d.y, d.z, ux};
-      acc.zero(k);
     }
     // phase 2: every element of the row's star, accumulated privately
     if (len > 0) {
@@ -933,6 +981,7 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
   nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
   if (st) return st;
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, h->rec);
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
   const size_t smem = lay.total();
@@ -1000,6 +1049,8 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
   }
   args.total_blocks = blocks;
   if (blocks == 0) return NSI_OK;
+  for (int k = 0; k < count; ++k)
+    pack_kernel<P><<<(hs[k]->n + 255) / 256, 256, 0, s>>>(args.item[k].m, args.item[k].f, hs[k]->rec);
   nsi_status st = set_gather_smem<P, false>();
   if (st) return st;
   const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_stars);
