@@ -216,6 +216,15 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOut
  */
 nsi_status nsi_device_status(NsiHandle* h, void* stream);
 
+/*
+ * Profiling hook: when both events (cudaEvent_t, created by the caller) are
+ * non-NULL, every later assemble call on this handle records `start` right
+ * before its main assembly kernel and `stop` right after it, on the call's
+ * stream, so that the caller can time that kernel alone (the per-call node
+ * packing and output zeroing stay outside the pair).  Pass NULLs to disable.
+ */
+nsi_status nsi_set_timing_events(NsiHandle* h, void* start, void* stop);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* nsi_last_error(void);
 

@@ -28,7 +28,7 @@ __all__ = [
     "load_library", "library_path", "exported_symbols",
     "nsi_assemble_create", "nsi_assemble_destroy", "nsi_csr_pattern", "nsi_csr_pattern_copy", "nsi_info",
     "nsi_assemble", "nsi_assemble_mode", "nsi_assemble_batched", "nsi_assemble_vjp", "nsi_assemble_host",
-    "nsi_residual", "nsi_device_status", "nsi_last_error", "nsi_abi_version",
+    "nsi_residual", "nsi_device_status", "nsi_set_timing_events", "nsi_last_error", "nsi_abi_version",
     "Assembler", "NsiResidual", "assemble_batched",
 ]
 
@@ -92,6 +92,7 @@ _SIGNATURES = {
     "nsi_assemble_host": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), _P],
     "nsi_residual": [_P, ctypes.POINTER(NsiFields), _P, _P],
     "nsi_device_status": [_P, _P],
+    "nsi_set_timing_events": [_P, _P, _P],
 }
 
 _lib = None
@@ -194,6 +195,10 @@ def nsi_assemble_host(h, fields: NsiFields, outputs: NsiOutputs, stream=None):
 
 def nsi_residual(h, fields: NsiFields, r_ptr, stream=None):
     _check(load_library().nsi_residual(h, ctypes.byref(fields), r_ptr, stream))
+
+
+def nsi_set_timing_events(h, start_event_ptr, stop_event_ptr):
+    _check(load_library().nsi_set_timing_events(h, start_event_ptr, stop_event_ptr))
 
 
 def nsi_device_status(h, stream=None):
@@ -351,6 +356,16 @@ class Assembler:
 
     def device_status(self, stream=None):
         nsi_device_status(self.handle, _stream_ptr(stream))
+
+    def set_timing_events(self, start=None, stop=None):
+        """Record torch.cuda.Event pair around the main assembly kernel of later calls (None: off)."""
+        if start is None or stop is None:
+            nsi_set_timing_events(self.handle, None, None)
+            return
+        for ev in (start, stop):
+            if not ev.cuda_event:  # torch creates the CUDA event on first record
+                ev.record()
+        nsi_set_timing_events(self.handle, ctypes.c_void_p(start.cuda_event), ctypes.c_void_p(stop.cuda_event))
 
 
 def assemble_batched(assemblers, us, rho=1.0, mu=1e-3, dt=1e-2, outs=None, stream=None):

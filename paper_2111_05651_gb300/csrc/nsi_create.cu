@@ -409,6 +409,14 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   return NSI_OK;
 }
 
+nsi_status nsi_set_timing_events(NsiHandle* h, void* start, void* stop) {
+  if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
+  if ((start == nullptr) != (stop == nullptr)) return fail(NSI_ERR_INVALID_ARG, "give both events or neither");
+  h->ev_start = static_cast<cudaEvent_t>(start);
+  h->ev_stop = static_cast<cudaEvent_t>(stop);
+  return NSI_OK;
+}
+
 nsi_status nsi_device_status(NsiHandle* h, void* stream) {
   if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

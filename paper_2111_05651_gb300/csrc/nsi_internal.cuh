@@ -122,6 +122,8 @@ struct NsiHandle {
   // in one or two DRAM sectors, rebuilt at the start of every gather call
   void* rec = nullptr;
   int rec_bytes = 0;
+  // optional profiling events around the main assembly kernel
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
   // device error word
   unsigned* err = nullptr;
   // staging for nsi_assemble_host (allocated on first use)

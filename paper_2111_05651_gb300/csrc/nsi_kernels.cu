@@ -959,13 +959,16 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
     if (st) return st;
     if (h->E == 0) return NSI_OK;
     const int64_t grid = (h->E + blk - 1) / blk;
+    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
     if (h->debug) elem_kernel<P, true, true><<<grid, blk, 0, s>>>(m, f, o, nullptr, h->E);
     else elem_kernel<P, true, false><<<grid, blk, 0, s>>>(m, f, o, nullptr, h->E);
+    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
     return check_launch("elem_kernel (atomic)");
   }
   if (mode == NSI_SCATTER_COLOR) {
     nsi_status st = zero_outputs<P>(h, o, s);
     if (st) return st;
+    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
     for (int c = 0; c < h->n_colors; ++c) {
       const int64_t off = h->color_off[c], cnt = h->color_off[c + 1] - off;
       if (cnt == 0) continue;
@@ -975,6 +978,7 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
       nsi_status st2 = check_launch("elem_kernel (colour)");
       if (st2) return st2;
     }
+    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
     return NSI_OK;
   }
   // row gather
@@ -985,8 +989,10 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
   const size_t smem = lay.total();
+  if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
   if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
   else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
+  if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
   return check_launch("gather_kernel");
 }
 
