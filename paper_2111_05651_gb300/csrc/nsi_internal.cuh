@@ -56,9 +56,10 @@ struct GatherPlan {
 //   nb0   T[4] per slot: edge vector d = x_j - x_i and u_x of the neighbour
 //   nb1   T[2] per slot: u_y, u_z
 //   acc   accumulators per slot (ab bytes): A and the three sums of c_i
-//   col   int32 per CSR entry, erow uint8 per CSR entry (its row), lb int32
-//         per row (row start inside the block's CSR range), star uint16 per
-//         word (copied as aligned pairs, so S + 2 of them)
+//   col   int32 per CSR entry; star uint16 per word (copied as aligned pairs,
+//         so S + 2 of them)
+// After the element loop, nb0 is reused to stage the finished values in CSR
+// order for the coalesced write-out.
 // Used identically by the host (launch size) and the kernel (carving).
 struct GatherSmem {
   int R, W, L, S, tb, ab;
@@ -68,9 +69,7 @@ struct GatherSmem {
   __host__ __device__ size_t nb1() const { return up16(nb0() + (size_t)4 * tb * N()); }
   __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
   __host__ __device__ size_t col() const { return up16(acc() + (size_t)ab * N()); }
-  __host__ __device__ size_t erow() const { return up16(col() + (size_t)4 * L); }
-  __host__ __device__ size_t lb() const { return up16(erow() + (size_t)L); }
-  __host__ __device__ size_t star() const { return up16(lb() + (size_t)4 * R); }
+  __host__ __device__ size_t star() const { return up16(col() + (size_t)4 * L); }
   __host__ __device__ size_t total() const { return up16(star() + (size_t)2 * (S + 2)); }
 };
 

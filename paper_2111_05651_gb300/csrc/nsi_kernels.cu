@@ -366,12 +366,11 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>* r) {
     a[k] = make_float4(r[0].v, r[1].v, r[2].v, r[3].v);
   }
-  __device__ __forceinline__ void write(int k, float kg, float* A, float* G, int64_t nnz, int64_t g) const {
+  // finished value of component C (0: A, 1..3: G_x..G_z) of slot k
+  template <int C>
+  __device__ __forceinline__ float value(int k, float kg) const {
     const float4 v = a[k];
-    A[g] = v.x;
-    G[g] = kg * v.y;
-    G[nnz + g] = kg * v.z;
-    G[2 * nnz + g] = kg * v.w;
+    return C == 0 ? v.x : kg * (C == 1 ? v.y : C == 2 ? v.z : v.w);
   }
 };
 template <>
@@ -422,15 +421,23 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     hi[k] = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
     lo[k] = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
   }
-  __device__ __forceinline__ void write(int k, float kg, double* A, double* G, int64_t nnz, int64_t g) const {
-    const float4 h = hi[k], l = lo[k];
+  template <int C>
+  __device__ __forceinline__ double value(int k, float kg) const {
+    const float4 h4 = hi[k], l4 = lo[k];
+    const float h = C == 0 ? h4.x : C == 1 ? h4.y : C == 2 ? h4.z : h4.w;
+    const float l = C == 0 ? l4.x : C == 1 ? l4.y : C == 2 ? l4.z : l4.w;
     Acc<NSI_MIXED_F32_ACC64> t;
-    t.hi = h.x; t.lo = l.x; store_acc(A + g, t);
-    // kg * (hi + lo), keeping the product error of the leading part
-    float p;
-    p = kg * h.y; t.hi = p; t.lo = fmaf(kg, h.y, -p) + kg * l.y; store_acc(G + g, t);
-    p = kg * h.z; t.hi = p; t.lo = fmaf(kg, h.z, -p) + kg * l.z; store_acc(G + nnz + g, t);
-    p = kg * h.w; t.hi = p; t.lo = fmaf(kg, h.w, -p) + kg * l.w; store_acc(G + 2 * nnz + g, t);
+    if (C == 0) {
+      t.hi = h;
+      t.lo = l;
+    } else {  // kg * (hi + lo), keeping the product error of the leading part
+      const float p = kg * h;
+      t.hi = p;
+      t.lo = fmaf(kg, h, -p) + kg * l;
+    }
+    double d;
+    store_acc(&d, t);
+    return d;
   }
 };
 template <>
@@ -464,12 +471,12 @@ struct AccSmem<NSI_FP64> {
     a0[k] = {r[0].v, r[1].v};
     a1[k] = {r[2].v, r[3].v};
   }
-  __device__ __forceinline__ void write(int k, double kg, double* A, double* G, int64_t nnz, int64_t g) const {
-    const T2<double> x = a0[k], y = a1[k];
-    A[g] = x.x;
-    G[g] = kg * x.y;
-    G[nnz + g] = kg * y.x;
-    G[2 * nnz + g] = kg * y.y;
+  template <int C>
+  __device__ __forceinline__ double value(int k, double kg) const {
+    if (C == 0) return a0[k].x;
+    if (C == 1) return kg * a0[k].y;
+    if (C == 2) return kg * a1[k].x;
+    return kg * a1[k].y;
   }
 };
 
@@ -592,8 +599,6 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   T2<T>* __restrict__ nb1 = reinterpret_cast<T2<T>*>(smem + lay.nb1());
   AccSmem<P> acc(smem + lay.acc(), lay.N());
   int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
-  uint8_t* erow = smem + lay.erow();
-  int32_t* lbs = reinterpret_cast<int32_t*>(smem + lay.lb());
   uint16_t* star = reinterpret_cast<uint16_t*>(smem + lay.star());
   const T kc = (T)(f.rho / 120.0);
   const T kmu = (T)(f.mu / 6.0);
@@ -614,8 +619,6 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
     s1 = m.star_ptr[i + 1] - sbase + soff;
     dp = m.diag_pos[i];
     uni = load_vec<T>(f.un, i);
-    lbs[t] = rs - base;
-    for (int k = rs - base; k < re - base; ++k) erow[k] = (uint8_t)t;
   }
   for (int k = t; k < L; k += R) cp_async4(&col[k], m.col_idx + base + k);
   {
@@ -737,12 +740,55 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
     }
   }
   __syncthreads();
-  // phase 3: coalesced write of the block's contiguous slice of A and G
+  // phase 3: the block's contiguous slice of A and G.  Every thread moves its
+  // own row's finished values into CSR order (nb0 reused as staging), then the
+  // block streams the slice out coalesced.
   Out* A = static_cast<Out*>(o.A);
   Out* G = static_cast<Out*>(o.G);
-  for (int k = t; k < L; k += R) {
-    const int r = erow[k];
-    acc.write((k - lbs[r]) * R + r, kg, A, G, m.nnz, (int64_t)base + k);
+  Out* stage = reinterpret_cast<Out*>(smem + lay.nb0());
+  Out* dst[4] = {A + base, G + base, G + m.nnz + base, G + 2 * m.nnz + base};
+  if constexpr (sizeof(Out) == sizeof(T4<T>) / 4 || P == NSI_FP64) {
+    // room for all four components at once
+    if (t < nrows) {
+      for (int q = 0, k = t; q < len; ++q, k += R) {
+        stage[lb + q] = acc.template value<0>(k, kg);
+        stage[L + lb + q] = acc.template value<1>(k, kg);
+        stage[2 * L + lb + q] = acc.template value<2>(k, kg);
+        stage[3 * L + lb + q] = acc.template value<3>(k, kg);
+      }
+    }
+    __syncthreads();
+    for (int k = t; k < L; k += R) {
+      dst[0][k] = stage[k];
+      dst[1][k] = stage[L + k];
+      dst[2][k] = stage[2 * L + k];
+      dst[3][k] = stage[3 * L + k];
+    }
+  } else {
+    // double values out of float slots: two components per round
+    if (t < nrows) {
+      for (int q = 0, k = t; q < len; ++q, k += R) {
+        stage[lb + q] = acc.template value<0>(k, kg);
+        stage[L + lb + q] = acc.template value<1>(k, kg);
+      }
+    }
+    __syncthreads();
+    for (int k = t; k < L; k += R) {
+      dst[0][k] = stage[k];
+      dst[1][k] = stage[L + k];
+    }
+    __syncthreads();
+    if (t < nrows) {
+      for (int q = 0, k = t; q < len; ++q, k += R) {
+        stage[lb + q] = acc.template value<2>(k, kg);
+        stage[L + lb + q] = acc.template value<3>(k, kg);
+      }
+    }
+    __syncthreads();
+    for (int k = t; k < L; k += R) {
+      dst[2][k] = stage[k];
+      dst[3][k] = stage[L + k];
+    }
   }
 }
 
