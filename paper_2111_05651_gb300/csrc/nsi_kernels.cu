@@ -36,11 +36,31 @@ struct MeshView {
   unsigned* err;
 };
 
+// Physical constants of the element formulas, precomputed on the host in
+// double (the float copies are rounded once): rho/120 (convection), mu/6
+// (viscous) and rho/(24 dt) (lumped mass).
 struct FieldView {
   const void* u[3];
   const void* un[3];
-  double rho, mu, dt;
+  double kc, kmu, kmass;
+  float kcf, kmuf, kmassf;
 };
+
+template <typename T>
+__device__ __forceinline__ T kc_of(const FieldView& f) {
+  if constexpr (sizeof(T) == 8) return f.kc;
+  else return f.kcf;
+}
+template <typename T>
+__device__ __forceinline__ T kmu_of(const FieldView& f) {
+  if constexpr (sizeof(T) == 8) return f.kmu;
+  else return f.kmuf;
+}
+template <typename T>
+__device__ __forceinline__ T kmass_of(const FieldView& f) {
+  if constexpr (sizeof(T) == 8) return f.kmass;
+  else return f.kmassf;
+}
 
 struct OutView {
   void* A;
@@ -73,9 +93,12 @@ static FieldView fields_of(const NsiFields* f) {
     v.u[k] = f->u[k];
     v.un[k] = f->u_n[k] ? f->u_n[k] : f->u[k];
   }
-  v.rho = f->rho;
-  v.mu = f->mu;
-  v.dt = f->dt;
+  v.kc = f->rho / 120.0;
+  v.kmu = f->mu / 6.0;
+  v.kmass = f->rho / (24.0 * f->dt);
+  v.kcf = (float)v.kc;
+  v.kmuf = (float)v.kmu;
+  v.kmassf = (float)v.kmass;
   return v;
 }
 
@@ -253,9 +276,9 @@ __global__ void __launch_bounds__(256) elem_kernel(MeshView m, FieldView f, OutV
   c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
   // Gauss-point velocity moments and element matrices
   const V3<T> S = add(add(u[0], u[1]), add(u[2], u[3]));
-  const T kc = (T)(f.rho / 120.0);
-  const T kv = (T)(f.mu / 6.0) * rcp(det);
-  const T km = det * (T)(f.rho / (24.0 * f.dt));
+  const T kc = kc_of<T>(f);
+  const T kv = kmu_of<T>(f) * rcp(det);
+  const T km = det * kmass_of<T>(f);
   const T kg = (T)(-1.0 / 24.0);
   Out* A = static_cast<Out*>(o.A);
   Out* G = static_cast<Out*>(o.G);
@@ -345,15 +368,20 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
   float4* __restrict__ a;
   __device__ __forceinline__ AccSmem(unsigned char* p, size_t) : a(reinterpret_cast<float4*>(p)) {}
   __device__ __forceinline__ void zero(int k) { a[k] = make_float4(0.f, 0.f, 0.f, 0.f); }
-  __device__ __forceinline__ void add3(int k1, int k2, int k3, float A1, float A2, float A3, float gx, float gy,
-                                       float gz) {
-    float4 v1 = a[k1], v2 = a[k2], v3 = a[k3];
-    v1.x += A1; v1.y += gx; v1.z += gy; v1.w += gz;
-    v2.x += A2; v2.y += gx; v2.z += gy; v2.w += gz;
-    v3.x += A3; v3.y += gx; v3.z += gy; v3.w += gz;
-    a[k1] = v1;
-    a[k2] = v2;
-    a[k3] = v3;
+  struct Slots {
+    float4 v1, v2, v3;
+  };
+  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const { return {a[k1], a[k2], a[k3]}; }
+  static __device__ __forceinline__ void update(Slots& s, float A1, float A2, float A3, float gx, float gy,
+                                                float gz) {
+    s.v1.x += A1; s.v1.y += gx; s.v1.z += gy; s.v1.w += gz;
+    s.v2.x += A2; s.v2.y += gx; s.v2.z += gy; s.v2.w += gz;
+    s.v3.x += A3; s.v3.y += gx; s.v3.z += gy; s.v3.w += gz;
+  }
+  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
+    a[k1] = s.v1;
+    a[k2] = s.v2;
+    a[k3] = s.v3;
   }
   // sums over the row's slots t, t + R, ... (len of them) except slot kd
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>* r) const {
@@ -395,19 +423,25 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     acc1(h.z, l.z, gy);
     acc1(h.w, l.w, gz);
   }
-  __device__ __forceinline__ void add3(int k1, int k2, int k3, float A1, float A2, float A3, float gx, float gy,
-                                       float gz) {
-    float4 h1 = hi[k1], h2 = hi[k2], h3 = hi[k3];
-    float4 l1 = lo[k1], l2 = lo[k2], l3 = lo[k3];
-    acc4(h1, l1, A1, gx, gy, gz);
-    acc4(h2, l2, A2, gx, gy, gz);
-    acc4(h3, l3, A3, gx, gy, gz);
-    hi[k1] = h1;
-    hi[k2] = h2;
-    hi[k3] = h3;
-    lo[k1] = l1;
-    lo[k2] = l2;
-    lo[k3] = l3;
+  struct Slots {
+    float4 h1, h2, h3, l1, l2, l3;
+  };
+  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const {
+    return {hi[k1], hi[k2], hi[k3], lo[k1], lo[k2], lo[k3]};
+  }
+  static __device__ __forceinline__ void update(Slots& s, float A1, float A2, float A3, float gx, float gy,
+                                                float gz) {
+    acc4(s.h1, s.l1, A1, gx, gy, gz);
+    acc4(s.h2, s.l2, A2, gx, gy, gz);
+    acc4(s.h3, s.l3, A3, gx, gy, gz);
+  }
+  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
+    hi[k1] = s.h1;
+    hi[k2] = s.h2;
+    hi[k3] = s.h3;
+    lo[k1] = s.l1;
+    lo[k2] = s.l2;
+    lo[k3] = s.l3;
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -450,15 +484,21 @@ struct AccSmem<NSI_FP64> {
     a0[k] = {0.0, 0.0};
     a1[k] = {0.0, 0.0};
   }
-  __device__ __forceinline__ void add3(int k1, int k2, int k3, double A1, double A2, double A3, double gx,
-                                       double gy, double gz) {
-    T2<double> x1 = a0[k1], x2 = a0[k2], x3 = a0[k3];
-    T2<double> y1 = a1[k1], y2 = a1[k2], y3 = a1[k3];
-    x1.x += A1; x1.y += gx; y1.x += gy; y1.y += gz;
-    x2.x += A2; x2.y += gx; y2.x += gy; y2.y += gz;
-    x3.x += A3; x3.y += gx; y3.x += gy; y3.y += gz;
-    a0[k1] = x1; a0[k2] = x2; a0[k3] = x3;
-    a1[k1] = y1; a1[k2] = y2; a1[k3] = y3;
+  struct Slots {
+    T2<double> x1, x2, x3, y1, y2, y3;
+  };
+  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const {
+    return {a0[k1], a0[k2], a0[k3], a1[k1], a1[k2], a1[k3]};
+  }
+  static __device__ __forceinline__ void update(Slots& s, double A1, double A2, double A3, double gx, double gy,
+                                                double gz) {
+    s.x1.x += A1; s.x1.y += gx; s.y1.x += gy; s.y1.y += gz;
+    s.x2.x += A2; s.x2.y += gx; s.y2.x += gy; s.y2.y += gz;
+    s.x3.x += A3; s.x3.y += gx; s.y3.x += gy; s.y3.y += gz;
+  }
+  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
+    a0[k1] = s.x1; a0[k2] = s.x2; a0[k3] = s.x3;
+    a1[k1] = s.y1; a1[k2] = s.y2; a1[k3] = s.y3;
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_FP64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -536,7 +576,9 @@ __device__ __forceinline__ bool star_ok(unsigned w, int len) {
   return !DEBUG || ((int)(w & 31) < len && (int)((w >> 5) & 31) < len && (int)((w >> 10) & 31) < len);
 }
 
-// the element loop of one row: 4 elements computed before their accumulation
+// the element loop of one row, software-pipelined one element deep: the
+// accumulator loads of element s are in flight while element s + 1 is
+// computed (it reads only the neighbour records), then element s is stored
 template <int P, bool DEBUG>
 __device__ __forceinline__ void star_loop(const uint16_t* __restrict__ star, int s0, int s1, int len,
                                           const T4<typename Prec<P>::T>* __restrict__ nb0,
@@ -544,37 +586,28 @@ __device__ __forceinline__ void star_loop(const uint16_t* __restrict__ star, int
                                           int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
                                           typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
   using T = typename Prec<P>::T;
-  int s = s0;
-  for (; s + 3 < s1; s += 4) {
-    const unsigned w0 = star[s], w1 = star[s + 1], w2 = star[s + 2], w3 = star[s + 3];
-    if (DEBUG && !(star_ok<P, DEBUG>(w0, len) && star_ok<P, DEBUG>(w1, len) && star_ok<P, DEBUG>(w2, len) &&
-                   star_ok<P, DEBUG>(w3, len))) {
+  if (DEBUG) {
+    bool ok = true;
+    for (int s = s0; s < s1; ++s) ok &= star_ok<P, DEBUG>(star[s], len);
+    if (!ok) {
       atomicOr(err, ERR_STAR);
-      continue;
+      return;
     }
-    const StarContrib<T> a = star_contrib<T>(w0, nb0, nb1, t, R, u2i, kc, kmu);
-    const StarContrib<T> b = star_contrib<T>(w1, nb0, nb1, t, R, u2i, kc, kmu);
-    const StarContrib<T> c = star_contrib<T>(w2, nb0, nb1, t, R, u2i, kc, kmu);
-    const StarContrib<T> d = star_contrib<T>(w3, nb0, nb1, t, R, u2i, kc, kmu);
-    acc.add3(a.k1, a.k2, a.k3, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
-    acc.add3(b.k1, b.k2, b.k3, b.A1, b.A2, b.A3, b.ci.x, b.ci.y, b.ci.z);
-    acc.add3(c.k1, c.k2, c.k3, c.A1, c.A2, c.A3, c.ci.x, c.ci.y, c.ci.z);
-    acc.add3(d.k1, d.k2, d.k3, d.A1, d.A2, d.A3, d.ci.x, d.ci.y, d.ci.z);
-    detsum.add(a.det);
-    detsum.add(b.det);
-    detsum.add(c.det);
-    detsum.add(d.det);
   }
-  for (; s < s1; ++s) {
-    const unsigned w0 = star[s];
-    if (!star_ok<P, DEBUG>(w0, len)) {
-      atomicOr(err, ERR_STAR);
-      continue;
-    }
-    const StarContrib<T> a = star_contrib<T>(w0, nb0, nb1, t, R, u2i, kc, kmu);
-    acc.add3(a.k1, a.k2, a.k3, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
+  if (s0 >= s1) return;
+  StarContrib<T> a = star_contrib<T>(star[s0], nb0, nb1, t, R, u2i, kc, kmu);
+  for (int s = s0 + 1; s < s1; ++s) {
+    typename AccSmem<P>::Slots v = acc.load3(a.k1, a.k2, a.k3);
+    const StarContrib<T> b = star_contrib<T>(star[s], nb0, nb1, t, R, u2i, kc, kmu);
+    AccSmem<P>::update(v, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
+    acc.store3(a.k1, a.k2, a.k3, v);
     detsum.add(a.det);
+    a = b;
   }
+  typename AccSmem<P>::Slots v = acc.load3(a.k1, a.k2, a.k3);
+  AccSmem<P>::update(v, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
+  acc.store3(a.k1, a.k2, a.k3, v);
+  detsum.add(a.det);
 }
 
 // one block of rows [r0, r0 + blockDim.x) of one mesh
@@ -600,9 +633,9 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   AccSmem<P> acc(smem + lay.acc(), lay.N());
   int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
   uint16_t* star = reinterpret_cast<uint16_t*>(smem + lay.star());
-  const T kc = (T)(f.rho / 120.0);
-  const T kmu = (T)(f.mu / 6.0);
-  const T kmass = (T)(f.rho / (24.0 * f.dt));
+  const T kc = kc_of<T>(f);
+  const T kmu = kmu_of<T>(f);
+  const T kmass = kmass_of<T>(f);
   const T kg = (T)(-1.0 / 24.0);
 
   // phase 0: the row's scalars and the entry -> row map; the block's column
@@ -860,9 +893,9 @@ __global__ void __launch_bounds__(256) vjp_kernel(MeshView m, FieldView f, const
     c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
     const V3<T> S = add(add(u[0], u[1]), add(u[2], u[3]));
     const V3<T> Ws = add(add(w[0], w[1]), add(w[2], w[3]));
-    const T kc = (T)(f.rho / 120.0);
-    const T kv = (T)(f.mu / 6.0) * rcp(det);
-    const T km = det * (T)(f.rho / (24.0 * f.dt));
+    const T kc = kc_of<T>(f);
+    const T kv = kmu_of<T>(f) * rcp(det);
+    const T km = det * kmass_of<T>(f);
     // Gu[k] as vectors over l
     V3<T> Gu[3];
     const T uk[4][3] = {{u[0].x, u[0].y, u[0].z}, {u[1].x, u[1].y, u[1].z}, {u[2].x, u[2].y, u[2].z},
@@ -946,9 +979,9 @@ __global__ void __launch_bounds__(256) residual_kernel(MeshView m, FieldView f, 
   const T det = dot(d1, c[1]);
   c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
   const V3<T> S = add(add(u[0], u[1]), add(u[2], u[3]));
-  const T kc = (T)(f.rho / 120.0);
-  const T kv = (T)(f.mu / 6.0) * rcp(det);
-  const T km = det * (T)(f.rho / (24.0 * f.dt));
+  const T kc = kc_of<T>(f);
+  const T kv = kmu_of<T>(f) * rcp(det);
+  const T km = det * kmass_of<T>(f);
   T* R = static_cast<T*>(rout);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
