@@ -211,6 +211,29 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOut
                              void* stream);
 
 /*
+ * Allocation-free assembly, for callers that may not allocate device memory
+ * while they run: code executing where cudaMalloc is not allowed or not
+ * wanted, such as a plugin whose device memory budget is fixed when it is
+ * loaded, a real-time loop that must not block on the allocator, or a host
+ * that hands every allocation to its own memory manager.  (The paper has no
+ * counterpart; this is an interface of this library only.)
+ *
+ * Same result as nsi_assemble in the row-gather mode, for a handle created
+ * beforehand.  The call allocates nothing: the per-call node records go to a
+ * scratch array compiled into the library (16 MiB, held by every GPU that
+ * loads the library until the process exits), so meshes of at most 524,288
+ * nodes in the mixed precisions and 262,144 nodes in FP64 are accepted;
+ * larger ones return NSI_ERR_UNSUPPORTED with a message giving both sizes.
+ * The first call on a device looks up the scratch's device address (one
+ * cudaGetSymbolAddress, no allocation); make that first call before any stream
+ * capture.  Every call on every handle shares the one scratch array and
+ * rewrites all of it that it reads, so nothing needs clearing between calls,
+ * but calls that overlap on the GPU (other streams, other threads) race on
+ * it: serialise them.
+ */
+nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream);
+
+/*
  * Synchronise `stream` and read the handle's device error word: NSI_OK, or
  * NSI_ERR_DEVICE_CHECK (bounds check fired; the word is then cleared).
  */

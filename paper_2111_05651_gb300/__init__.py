@@ -93,6 +93,7 @@ _SIGNATURES = {
     "nsi_residual": [_P, ctypes.POINTER(NsiFields), _P, _P],
     "nsi_device_status": [_P, _P],
     "nsi_set_timing_events": [_P, _P, _P],
+    "nsi_assemble_noalloc": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), _P],
 }
 
 _lib = None

@@ -13,6 +13,7 @@
 //
 // Formulas: see the element-arithmetic comment in nsi_internal.cuh.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -1181,6 +1182,46 @@ int gather_kernel_regs(int precision) {
   return e == cudaSuccess ? a.numRegs : 96;
 }
 
+// ------------------------------------------------ allocation-free variant ---
+// Scratch of nsi_assemble_noalloc: room for the per-call node records of one
+// mesh (32 bytes per node in the mixed modes, 64 in FP64).  It lives in the
+// library's own device image, so every GPU that loads the library holds these
+// 16 MiB until the process exits, and no call ever allocates it.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of the scratch for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device, with that device current, and cached.
+static nsi_status noalloc_scratch(int dev, void** out) {
+  constexpr int MAX_DEV = 64;
+  static std::mutex mu;
+  static void* addr[MAX_DEV] = {};
+  if (dev < 0 || dev >= MAX_DEV) return fail(NSI_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    NSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return NSI_OK;
+}
+
+template <int P>
+static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const OutView& o, void* scratch,
+                                     cudaStream_t s) {
+  nsi_status st = set_gather_smem<P, false>();
+  if (st) return st;
+  MeshView m = view_of(h);
+  m.rec = scratch;
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, scratch);
+  const int R = h->plan.rows_per_block;
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
+  gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay);
+  return check_launch("gather_kernel (no-alloc)");
+}
+
 }  // namespace nsi
 
 using namespace nsi;
@@ -1238,6 +1279,35 @@ nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->precision == NSI_FP64) return residual_p<NSI_FP64>(h, fv, r, s);
   return residual_p<NSI_MIXED_F32_ACC32>(h, fv, r, s);
+}
+
+nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {
+  nsi_status st = check_call(h, f, o);
+  if (st) return st;
+  if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "the allocation-free call needs the row-gather mode (rows of at most 32 entries)");
+  const size_t rec = h->precision == NSI_FP64 ? 64 : 32;
+  if ((size_t)h->n * rec > NOALLOC_SCRATCH_BYTES) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "mesh too large for the allocation-free call: %lld nodes need %zu bytes of scratch, the static "
+             "scratch holds %zu (%zu nodes at %zu bytes each)",
+             (long long)h->n, (size_t)h->n * rec, NOALLOC_SCRATCH_BYTES, NOALLOC_SCRATCH_BYTES / rec, rec);
+    return fail(NSI_ERR_UNSUPPORTED, buf);
+  }
+  int dev = 0;
+  NSI_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");
+  void* scratch = nullptr;
+  st = noalloc_scratch(dev, &scratch);
+  if (st) return st;
+  const FieldView fv = fields_of(f);
+  const OutView ov{o->A_val, o->G_val, o->rhs};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (h->precision) {
+    case NSI_FP64: return assemble_noalloc_p<NSI_FP64>(h, fv, ov, scratch, s);
+    case NSI_MIXED_F32_ACC64: return assemble_noalloc_p<NSI_MIXED_F32_ACC64>(h, fv, ov, scratch, s);
+    default: return assemble_noalloc_p<NSI_MIXED_F32_ACC32>(h, fv, ov, scratch, s);
+  }
 }
 
 nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {
