@@ -156,7 +156,9 @@ nsi_status nsi_csr_pattern_copy(const NsiHandle* h, int32_t* row_ptr, int32_t* c
 typedef struct {
     int64_t n_nodes, n_elems, nnz;
     int32_t n_colors, max_row, precision, scatter;
-    int64_t device_bytes; /* device memory owned by the handle */
+    int64_t device_bytes;   /* device memory owned by the handle */
+    int32_t rows_per_block; /* row-gather launch shape in use (0: mode unavailable) */
+    int32_t n_plans;        /* row-gather launch shapes available */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 
@@ -238,6 +240,23 @@ nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutpu
  * NSI_ERR_DEVICE_CHECK (bounds check fired; the word is then cleared).
  */
 nsi_status nsi_device_status(NsiHandle* h, void* stream);
+
+/*
+ * Launch autotuner (project-written): times every available launch choice on
+ * this mesh with the given fields and outputs -- the row-gather kernel at each
+ * rows-per-block shape that fits shared memory, the colouring kernel and the
+ * atomic kernel -- `reps` calls each after one warm-up call, keeps the fastest
+ * as the handle's default, and reports it.  Synchronises `stream`; overwrites
+ * the outputs.  chosen_scatter / chosen_rows may be NULL.
+ */
+nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t reps, void* stream,
+                        int32_t* chosen_scatter, int32_t* chosen_rows);
+
+/*
+ * Set the handle's default scatter mode and row-gather shape (rows per block;
+ * 0 keeps the current one), e.g. from a cached autotuning result.
+ */
+nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block);
 
 /*
  * Profiling hook: when both events (cudaEvent_t, created by the caller) are

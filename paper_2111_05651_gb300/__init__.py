@@ -28,7 +28,8 @@ __all__ = [
     "load_library", "library_path", "exported_symbols",
     "nsi_assemble_create", "nsi_assemble_destroy", "nsi_csr_pattern", "nsi_csr_pattern_copy", "nsi_info",
     "nsi_assemble", "nsi_assemble_mode", "nsi_assemble_batched", "nsi_assemble_vjp", "nsi_assemble_host",
-    "nsi_residual", "nsi_device_status", "nsi_set_timing_events", "nsi_last_error", "nsi_abi_version",
+    "nsi_residual", "nsi_device_status", "nsi_set_timing_events", "nsi_autotune", "nsi_set_launch",
+    "nsi_last_error", "nsi_abi_version",
     "Assembler", "NsiResidual", "assemble_batched",
 ]
 
@@ -74,7 +75,8 @@ class NsiOutputs(ctypes.Structure):
 class NsiInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("n_colors", ctypes.c_int32), ("max_row", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("scatter", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("scatter", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("rows_per_block", ctypes.c_int32),
+                ("n_plans", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -94,6 +96,9 @@ _SIGNATURES = {
     "nsi_device_status": [_P, _P],
     "nsi_set_timing_events": [_P, _P, _P],
     "nsi_assemble_noalloc": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), _P],
+    "nsi_autotune": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), ctypes.c_int32, _P,
+                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "nsi_set_launch": [_P, ctypes.c_int32, ctypes.c_int32],
 }
 
 _lib = None
@@ -196,6 +201,17 @@ def nsi_assemble_host(h, fields: NsiFields, outputs: NsiOutputs, stream=None):
 
 def nsi_residual(h, fields: NsiFields, r_ptr, stream=None):
     _check(load_library().nsi_residual(h, ctypes.byref(fields), r_ptr, stream))
+
+
+def nsi_autotune(h, fields: NsiFields, outputs: NsiOutputs, reps=5, stream=None):
+    sc, rows = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().nsi_autotune(h, ctypes.byref(fields), ctypes.byref(outputs), reps, stream,
+                                       ctypes.byref(sc), ctypes.byref(rows)))
+    return sc.value, rows.value
+
+
+def nsi_set_launch(h, scatter, rows_per_block):
+    _check(load_library().nsi_set_launch(h, scatter, rows_per_block))
 
 
 def nsi_set_timing_events(h, start_event_ptr, stop_event_ptr):
@@ -357,6 +373,47 @@ class Assembler:
 
     def device_status(self, stream=None):
         nsi_device_status(self.handle, _stream_ptr(stream))
+
+    def info(self):
+        return nsi_info(self.handle)
+
+    def autotune(self, u, rho=1.0, mu=1e-3, dt=1e-2, reps=5, cache=None, stream=None):
+        """Pick scatter mode and rows-per-block by timing them on this mesh.
+
+        With ``cache`` (a JSON file path), a choice made before for the same GPU,
+        precision and mesh size is reused without timing; new choices are added.
+        Returns (scatter mode name, rows per block).
+        """
+        import json
+        import torch
+
+        key = "|".join([torch.cuda.get_device_name(self.device), str(self.precision), str(self.n), str(self.E),
+                        str(self.nnz), str(self.max_row)])
+        db = {}
+        if cache and os.path.exists(cache):
+            try:
+                with open(cache) as fh:
+                    db = json.load(fh)
+            except (OSError, ValueError):
+                db = {}
+        names = {v: k for k, v in SCATTERS.items()}
+        if key in db:
+            sc, rows = db[key]["scatter"], db[key]["rows_per_block"]
+            nsi_set_launch(self.handle, SCATTERS[sc], rows)
+        else:
+            f, keep = self.fields(u, None, rho, mu, dt)
+            A, G, rhs = self.empty_outputs()
+            o = NsiOutputs(A.data_ptr(), G.data_ptr(), rhs.data_ptr())
+            code, rows = nsi_autotune(self.handle, f, o, reps, _stream_ptr(stream))
+            sc = names[code]
+            if cache:
+                db[key] = {"scatter": sc, "rows_per_block": rows}
+                tmp = f"{cache}.{os.getpid()}.tmp"
+                with open(tmp, "w") as fh:
+                    json.dump(db, fh, indent=1)
+                os.replace(tmp, cache)
+        self.scatter = nsi_info(self.handle).scatter
+        return sc, rows
 
     def set_timing_events(self, start=None, stop=None):
         """Record torch.cuda.Event pair around the main assembly kernel of later calls (None: off)."""

@@ -270,6 +270,12 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
       int blocks = (int)std::min<size_t>({smem_sm / (sm + 1024), (size_t)32, (size_t)(2048 / R),
                                           (size_t)(65536 / (R * regs))});
       const int warps = blocks * R / 32;
+      GatherPlan cand;
+      cand.rows_per_block = R;
+      cand.max_block_entries = (int)mL;
+      cand.max_block_stars = (int)mS;
+      cand.n_blocks = (n + R - 1) / R;
+      h->plans[h->n_plans++] = cand;
       if (warps > best_warps) {
         best_warps = warps;
         chosen = R;
@@ -406,6 +412,22 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->precision = h->precision;
   info->scatter = h->scatter;
   info->device_bytes = h->device_bytes;
+  info->rows_per_block = h->plan.rows_per_block;
+  info->n_plans = h->n_plans;
+  return NSI_OK;
+}
+
+nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block) {
+  if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
+  if (scatter < NSI_SCATTER_AUTO || scatter > NSI_SCATTER_GATHER) return fail(NSI_ERR_INVALID_ARG, "unknown scatter mode");
+  if (scatter == NSI_SCATTER_GATHER && !h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode not available for this mesh");
+  if (rows_per_block != 0) {
+    int k = 0;
+    while (k < h->n_plans && h->plans[k].rows_per_block != rows_per_block) ++k;
+    if (k == h->n_plans) return fail(NSI_ERR_UNSUPPORTED, "no launch plan with that many rows per block");
+    h->plan = h->plans[k];
+  }
+  if (scatter != NSI_SCATTER_AUTO) h->scatter = scatter;
   return NSI_OK;
 }
 

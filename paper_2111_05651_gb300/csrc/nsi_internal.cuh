@@ -111,7 +111,9 @@ struct NsiHandle {
   int32_t* star_ptr = nullptr;  // [n+1]
   uint16_t* star = nullptr;     // [star_ptr[n]]
   uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row
-  nsi::GatherPlan plan;
+  nsi::GatherPlan plan;         // the launch plan in use
+  nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
+  int n_plans = 0;
   // coordinates: double4 for FP64, float4 hi + float4 lo for the mixed modes
   nsi::D4* xyz64 = nullptr;
   float4* xyz_hi = nullptr;

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "nsi_internal.cuh"
 
@@ -1308,6 +1309,60 @@ nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutpu
     case NSI_MIXED_F32_ACC64: return assemble_noalloc_p<NSI_MIXED_F32_ACC64>(h, fv, ov, scratch, s);
     default: return assemble_noalloc_p<NSI_MIXED_F32_ACC32>(h, fv, ov, scratch, s);
   }
+}
+
+nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t reps, void* stream,
+                        int32_t* chosen_scatter, int32_t* chosen_rows) {
+  nsi_status st = check_call(h, f, o);
+  if (st) return st;
+  if (reps < 1 || reps > 1000) return fail(NSI_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  NSI_CUDA(cudaEventCreate(&e0));
+  NSI_CUDA(cudaEventCreate(&e1));
+  struct Cand {
+    int scatter, plan;
+  };
+  std::vector<Cand> cands;
+  if (h->gather_ok)
+    for (int k = 0; k < h->n_plans; ++k) cands.push_back({NSI_SCATTER_GATHER, k});
+  cands.push_back({NSI_SCATTER_COLOR, -1});
+  cands.push_back({NSI_SCATTER_ATOMIC, -1});
+  const GatherPlan saved = h->plan;
+  float best = 1e30f;
+  Cand pick{h->scatter, -1};
+  cudaEvent_t ev0 = h->ev_start, ev1 = h->ev_stop;
+  h->ev_start = h->ev_stop = nullptr;
+  for (const Cand& c : cands) {
+    if (c.plan >= 0) h->plan = h->plans[c.plan];
+    st = assemble_dispatch(h, f, o, c.scatter, s);  // warm-up
+    if (st) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && !st; ++r) st = assemble_dispatch(h, f, o, c.scatter, s);
+    cudaEventRecord(e1, s);
+    if (st) break;
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ce, "cudaEventSynchronize in autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  h->ev_start = ev0;
+  h->ev_stop = ev1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->plan = pick.plan >= 0 ? h->plans[pick.plan] : saved;
+  if (st) return st;
+  h->scatter = pick.scatter;
+  if (chosen_scatter) *chosen_scatter = pick.scatter;
+  if (chosen_rows) *chosen_rows = pick.scatter == NSI_SCATTER_GATHER ? h->plan.rows_per_block : 0;
+  return NSI_OK;
 }
 
 nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {

@@ -46,7 +46,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(nsi.NsiOptions) == 32
     assert ctypes.sizeof(nsi.NsiFields) == 72
     assert ctypes.sizeof(nsi.NsiOutputs) == 24
-    assert ctypes.sizeof(nsi.NsiInfo) == 48
+    assert ctypes.sizeof(nsi.NsiInfo) == 56
 
 
 def test_null_arguments_rejected_without_gpu():
@@ -90,6 +90,9 @@ def test_calls_on_null_handle():
     assert lib.nsi_csr_pattern(None, None, None, None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_info(None, None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_device_status(None, None) == nsi.NSI_ERR_INVALID_ARG
+    assert lib.nsi_set_launch(None, 0, 0) == nsi.NSI_ERR_INVALID_ARG
+    assert lib.nsi_autotune(None, ctypes.byref(f), ctypes.byref(o), 3, None, None, None) == nsi.NSI_ERR_INVALID_ARG
+    assert lib.nsi_assemble_noalloc(None, ctypes.byref(f), ctypes.byref(o), None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_assemble_destroy(None) == nsi.NSI_OK
     hs = (ctypes.c_void_p * 1)()
     assert lib.nsi_assemble_batched(hs, None, None, -1, None) == nsi.NSI_ERR_INVALID_ARG
