@@ -33,6 +33,9 @@ import numpy as np  # noqa: E402
 import meshgen  # noqa: E402
 
 WORKLOADS = {
+    "batch64": "64 jittered Kuhn cubes, N ~ U{10..60} hexes a side (seeded), one persistent batched launch "
+               "captured with the velocity update in a CUDA graph and replayed every step",
+    "adjoint50": "Kuhn cube 50^3 hexes, 750,000 tets, jitter 15% h: vector-Jacobian product of R = A(u)u - b",
     "cube100": "Kuhn cube 100^3 hexes, 6,000,000 tets, 1,030,301 nodes, jitter 15% h, random numbering, seed 1",
     "cube8": "Kuhn cube 8^3 hexes, 3,072 tets, 729 nodes, natural numbering, seed 0",
     "cube200_rcm": "Kuhn cube 200^3 hexes, 48,000,000 tets, 8,120,601 nodes, jitter 15% h, RCM numbering, 5% noise",
@@ -192,7 +195,7 @@ def run_reference(args, world, rank):
         return
     import oracle
 
-    mesh, u = meshgen.config_mesh(args.workload)
+    mesh, u = meshgen.config_mesh(args.workload if args.workload in meshgen.CONFIGS else "cube100")
     n_s = min(args.ref_sample, mesh.n_elems)
     ln = mesh.lnods[:n_s]
     csr = oracle.pattern(mesh.n_nodes, ln)
@@ -387,6 +390,102 @@ def run_gpu(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, world, rank, local):
+    """64 meshes per step: velocity update + batched assembly replayed from one CUDA graph."""
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    torch.cuda.set_device(local)
+    nsi.load_library()
+    meshes = meshgen.batch_meshes()
+    prec = args.precision
+    asms = [nsi.Assembler(m.coord, m.lnods, precision=prec) for m, _ in meshes]
+    vt = torch.float64 if prec == "fp64" else torch.float32
+    base = [torch.as_tensor(u.T.copy()).cuda().to(vt) for _, u in meshes]
+    cache = os.path.join(ROOT, "paper_2111_05651_gb300", "_build", "autotune_cache.json") if args.autotune else None
+    tuned = {}
+    if args.autotune:
+        for a, b in zip(asms, base):
+            r = a.autotune(b, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, cache=cache)
+            tuned[r] = tuned.get(r, 0) + 1
+    cur = [b.clone() for b in base]
+    outs = [a.empty_outputs() for a in asms]
+    step = torch.zeros(1, device="cuda", dtype=vt)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        nsi.assemble_batched(asms, cur, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, outs=outs)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step.add_(1.0)
+        for c, b in zip(cur, base):  # u(t) = u0 cos(2 pi 0.01 t): the in-graph velocity update
+            c.copy_(b * torch.cos(0.06283185307179587 * step))
+        nsi.assemble_batched(asms, cur, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, outs=outs)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    E = sum(m.n_elems for m, _ in meshes)
+    steps = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = allreduce_max(e0.elapsed_time(e1) / steps, world)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "tet elements assembled/s", "value": world * E / (ms * 1e-3), "unit": "elements/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch64"], "meshes": len(meshes), "elements": E,
+                       "precision": prec, "launches_per_step": "1 batched + 64 pack + velocity update",
+                       "autotuned": {f"{k[0]}/{k[1]}": v for k, v in tuned.items()} or None,
+                       "l2": "working set (outputs of all meshes) > L2; no flush between replays"},
+        }), flush=True)
+
+
+def run_adjoint(args, world, rank, local):
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    torch.cuda.set_device(local)
+    nsi.load_library()
+    mesh, u = meshgen.config_mesh("cube50")
+    w = meshgen.gaussian_weights(mesh.n_nodes, np.random.default_rng(40))
+    res = {}
+    for prec in ("fp64", "mixed64"):
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec)
+        vt = torch.float64 if prec == "fp64" else torch.float32
+        ut = torch.as_tensor(u.T.copy()).cuda().to(vt)
+        wt = torch.as_tensor(w.T.copy()).cuda().to(vt)
+        for _ in range(args.warmup):
+            asm.vjp(ut, wt, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            asm.vjp(ut, wt, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        asm.close()
+    if rank == 0:
+        print(json.dumps({"metric": "tet elements differentiated/s (VJP of the assembled residual)",
+                          "value": res["mixed64"]["elements_per_s"], "unit": "elements/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["mixed64"]["ms"],
+                          "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": WORKLOADS["adjoint50"], "elements": mesh.n_elems},
+                          "modes": res}), flush=True)
+
+
 def run_profile(args):
     """Untimed assemblies for an external profiler: per precision, 3 calls."""
     import torch
@@ -421,6 +520,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="time only the main precision")
+    ap.add_argument("--autotune", action="store_true", help="batch64: autotune launch shapes (cached)")
     ap.add_argument("--profile-run", default=None, metavar="PRECS",
                     help="no timing: 3 assembly calls per listed precision (for ncu)")
     args = ap.parse_args()
@@ -432,6 +532,10 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "batch64":
+            run_batch(args, world, rank, local)
+        elif args.workload == "adjoint50":
+            run_adjoint(args, world, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:
