@@ -157,7 +157,8 @@ typedef struct {
     int64_t n_nodes, n_elems, nnz;
     int32_t n_colors, max_row, precision, scatter;
     int64_t device_bytes;   /* device memory owned by the handle */
-    int32_t rows_per_block; /* row-gather launch shape in use (0: mode unavailable) */
+    int32_t rows_per_block; /* row-gather launch shape in use: rows per block of the per-row
+                               star kernel, -1 for the edge-fan kernel, 0 if unavailable */
     int32_t n_plans;        /* row-gather launch shapes available */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
@@ -245,16 +246,19 @@ nsi_status nsi_device_status(NsiHandle* h, void* stream);
  * Launch autotuner (project-written): times every available launch choice on
  * this mesh with the given fields and outputs -- the row-gather kernel at each
  * rows-per-block shape that fits shared memory, the colouring kernel and the
- * atomic kernel -- `reps` calls each after one warm-up call, keeps the fastest
- * as the handle's default, and reports it.  Synchronises `stream`; overwrites
- * the outputs.  chosen_scatter / chosen_rows may be NULL.
+ * atomic kernel, and the edge-fan row-gather kernel where the mesh has its map
+ * -- `reps` calls each after one warm-up call, keeps the fastest as the
+ * handle's default, and reports it (chosen_rows as in nsi_set_launch).
+ * Synchronises `stream`; overwrites the outputs.  Either output may be NULL.
  */
 nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t reps, void* stream,
                         int32_t* chosen_scatter, int32_t* chosen_rows);
 
 /*
- * Set the handle's default scatter mode and row-gather shape (rows per block;
- * 0 keeps the current one), e.g. from a cached autotuning result.
+ * Set the handle's default scatter mode and row-gather kernel: rows_per_block
+ * > 0 selects the per-row star kernel with that many rows per block, -1 the
+ * edge-fan kernel (one thread per CSR entry), 0 keeps the current choice; e.g.
+ * to apply a cached autotuning result.
  */
 nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block);
 

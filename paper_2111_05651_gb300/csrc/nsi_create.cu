@@ -66,6 +66,8 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->star_ptr);
   cudaFree(h->star);
   cudaFree(h->diag_pos);
+  cudaFree(h->fan);
+  cudaFree(h->fan_blk);
   cudaFree(h->xyz64);
   cudaFree(h->xyz_hi);
   cudaFree(h->xyz_lo);
@@ -191,6 +193,81 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     });
   }
 
+  // 4b. edge-fan map: per off-diagonal entry (i, j) the ring of nodes around the edge
+  std::vector<uint32_t> fan;
+  std::vector<int32_t> fan_blk;
+  h->fan_ok = h->gather_ok && max_row <= FAN_MAX_ROW;
+  if (h->fan_ok) {
+    fan.assign(nnz, 0u);
+    std::atomic<bool> bad{false};
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+      int nxt[FAN_MAX_ROW], prv[FAN_MAX_ROW];
+      for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); ++i) {
+        const int len = (int)row_len[i];
+        const int dp = diag[i];
+        for (int q = 0; q < len; ++q) {
+          if (q == dp) continue;
+          for (int v = 0; v < len; ++v) nxt[v] = prv[v] = -1;
+          int edges = 0;
+          bool ok = true;
+          // every element of the star holding q: (i, q, k, l) as an even permutation
+          for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
+            const unsigned w = star[t];
+            const int p1 = w & 31, p2 = (w >> 5) & 31, p3 = (w >> 10) & 31;
+            int k, l;
+            if (p1 == q) { k = p2; l = p3; }
+            else if (p2 == q) { k = p3; l = p1; }
+            else if (p3 == q) { k = p1; l = p2; }
+            else continue;
+            if (nxt[k] != -1 || prv[l] != -1) { ok = false; break; }
+            nxt[k] = l;
+            prv[l] = k;
+            ++edges;
+          }
+          if (!ok || edges == 0) { bad = true; break; }
+          // chain: start at a node without predecessor (open fan) or anywhere (closed)
+          int start = -1, nodes = 0;
+          for (int v = 0; v < len; ++v)
+            if (nxt[v] != -1 && prv[v] == -1) start = v;
+          const bool closed = start == -1;
+          if (closed)
+            for (int v = 0; v < len && start == -1; ++v)
+              if (nxt[v] != -1) start = v;
+          uint32_t word = 0;
+          int v = start;
+          while (v != -1 && nodes <= FAN_MAX_RING) {
+            if (nodes < FAN_MAX_RING) word |= (uint32_t)v << (4 * nodes);
+            ++nodes;
+            v = nxt[v];
+            if (v == start) break;
+          }
+          if (nodes > FAN_MAX_RING || edges != (closed ? nodes : nodes - 1)) { bad = true; break; }
+          word |= (uint32_t)nodes << 24;
+          if (closed) word |= 1u << 27;
+          fan[rp64[i] + q] = word;
+        }
+      }
+    });
+    if (bad.load()) {
+      h->fan_ok = false;
+      fan.clear();
+    }
+  }
+  if (h->fan_ok) {
+    // blocks of whole rows holding at most FAN_BLOCK entries
+    fan_blk.push_back(0);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (acc + row_len[i] > FAN_BLOCK) {
+        fan_blk.push_back((int32_t)i);
+        acc = 0;
+      }
+      acc += row_len[i];
+    }
+    fan_blk.push_back((int32_t)n);
+    h->fan_blocks = (int64_t)fan_blk.size() - 1;
+  }
+
   // 5. greedy element colouring: no two elements of one colour share a node
   std::vector<int32_t> color(E);
   {
@@ -296,6 +373,13 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   if ((st = dev_upload(h, &h->col_idx, col.data(), nnz, s))) return st;
   if ((st = dev_upload(h, &h->lnods, reinterpret_cast<const int4*>(ln.data()), E, s))) return st;
   if ((st = dev_upload(h, &h->color_elems, color_elems.data(), E, s))) return st;
+  if (h->fan_ok) {
+    // available to the autotuner / nsi_set_launch; the per-row star kernel stays
+    // the default (each element is evaluated 3 times per row in the fan kernel,
+    // which costs more than the shared-memory accumulation it saves on GB300)
+    if ((st = dev_upload(h, &h->fan, fan.data(), fan.size(), s))) return st;
+    if ((st = dev_upload(h, &h->fan_blk, fan_blk.data(), fan_blk.size(), s))) return st;
+  }
   if (h->gather_ok) {
     if ((st = dev_upload(h, &h->star_ptr, star_ptr.data(), n + 1, s))) return st;
     if ((st = dev_upload(h, &h->star, star.data(), star.size(), s))) return st;
@@ -412,7 +496,7 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->precision = h->precision;
   info->scatter = h->scatter;
   info->device_bytes = h->device_bytes;
-  info->rows_per_block = h->plan.rows_per_block;
+  info->rows_per_block = h->use_fan ? -1 : h->plan.rows_per_block;
   info->n_plans = h->n_plans;
   return NSI_OK;
 }
@@ -421,11 +505,15 @@ nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block)
   if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
   if (scatter < NSI_SCATTER_AUTO || scatter > NSI_SCATTER_GATHER) return fail(NSI_ERR_INVALID_ARG, "unknown scatter mode");
   if (scatter == NSI_SCATTER_GATHER && !h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode not available for this mesh");
-  if (rows_per_block != 0) {
+  if (rows_per_block == -1) {
+    if (!h->fan_ok) return fail(NSI_ERR_UNSUPPORTED, "no edge-fan map for this mesh");
+    h->use_fan = true;
+  } else if (rows_per_block != 0) {
     int k = 0;
     while (k < h->n_plans && h->plans[k].rows_per_block != rows_per_block) ++k;
     if (k == h->n_plans) return fail(NSI_ERR_UNSUPPORTED, "no launch plan with that many rows per block");
     h->plan = h->plans[k];
+    h->use_fan = false;
   }
   if (scatter != NSI_SCATTER_AUTO) h->scatter = scatter;
   return NSI_OK;

@@ -36,6 +36,20 @@ enum : unsigned { ERR_BAD_INDEX = 1u, ERR_NOT_IN_PATTERN = 2u, ERR_STAR = 4u };
 constexpr int STAR_BITS = 5;
 constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
 
+// Edge-fan map: for every off-diagonal CSR entry (i, j), the ring of nodes
+// around the edge (i, j) -- the other two nodes of every element containing
+// both i and j, chained in cyclic order so that consecutive ring nodes k, l
+// form the positively oriented element (i, j, k, l) -- as positions inside
+// row i.  One 32-bit word per entry: ring positions in bits 0..23 (4 bits
+// each, up to 6 of them), ring size in bits 24..26, bit 27 set when the ring
+// is closed (interior edge: as many elements as ring nodes) and clear when it
+// is open (boundary edge: one element fewer).  The diagonal entry has word 0.
+// Meshes with rows longer than 16 entries, rings longer than 6 nodes or
+// non-manifold edge fans do not get the map and use the per-row star kernel.
+constexpr int FAN_MAX_ROW = 16;
+constexpr int FAN_MAX_RING = 6;
+constexpr int FAN_BLOCK = 256;  // CSR entries (threads) per fan block
+
 // vector types with explicit alignment (CUDA 13 deprecates the unsuffixed double4)
 struct alignas(32) D4 {
   double x, y, z, w;
@@ -111,6 +125,12 @@ struct NsiHandle {
   int32_t* star_ptr = nullptr;  // [n+1]
   uint16_t* star = nullptr;     // [star_ptr[n]]
   uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row
+  // edge-fan map (one word per CSR entry) and its block partition of the rows
+  bool fan_ok = false;
+  uint32_t* fan = nullptr;      // [nnz]
+  int32_t* fan_blk = nullptr;   // [fan_blocks + 1] first row of every fan block
+  int64_t fan_blocks = 0;
+  bool use_fan = false;         // row-gather mode runs the edge-fan kernel
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
   int n_plans = 0;

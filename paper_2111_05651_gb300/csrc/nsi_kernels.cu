@@ -35,6 +35,8 @@ struct MeshView {
   const float4* __restrict__ xyz_hi;
   const float4* __restrict__ xyz_lo;
   const void* __restrict__ rec;
+  const uint32_t* __restrict__ fan;
+  const int32_t* __restrict__ fan_blk;
   unsigned* err;
 };
 
@@ -85,6 +87,8 @@ static MeshView view_of(const NsiHandle* h) {
   m.xyz_hi = h->xyz_hi;
   m.xyz_lo = h->xyz_lo;
   m.rec = h->rec;
+  m.fan = h->fan;
+  m.fan_blk = h->fan_blk;
   m.err = h->err;
   return m;
 }
@@ -827,6 +831,273 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   }
 }
 
+// ------------------------------------------------------ edge-fan kernel ---
+// One thread per CSR entry (i, j) of a block of whole rows.  An off-diagonal
+// entry walks the ring of nodes k_0 .. k_{r-1} around the edge (i, j): the
+// elements containing the edge are (i, j, k_m, k_{m+1}), positively oriented.
+// With i as the origin and q_m = d_j x d_{k_m}, such an element has
+//   c_j = d_{k_m} x d_{k_{m+1}},  c_i = -(c_j + q_m - q_{m+1}),  det = d_j . c_j
+// (c_{k_m} = -q_{m+1} and c_{k_{m+1}} = q_m come for free from the ring), and
+// adds w . c_j to A(i, j), c_i to the pressure-gradient sum and det to the
+// lumped mass sum, with w = rho/120 (2 u_i + u_j + u_{k_m} + u_{k_{m+1}}) +
+// mu/(6 det) c_i.  All sums stay in registers.  The diagonal entry receives
+// the row totals through a tree reduction in shared memory:
+//   A(i,i) = M_i - sum_{j != i} A(i,j), G(i,i) = 1/3 sum_{j != i} G(i,j),
+//   M_i = rho/(24 dt) * 1/3 sum_{j != i} sum_fan det
+// (every element of the star appears in the fans of its three other nodes).
+// Every thread then writes its own entry: the block's slice of A and G goes
+// out coalesced.
+
+// shared-memory layout of a fan block (T entries)
+template <int P>
+struct FanSmem {
+  using T = typename Prec<P>::T;
+  static constexpr size_t rec() { return 0; }                                        // T4 [T] x 2
+  static constexpr size_t rp(int Tn) { return 2 * sizeof(T4<T>) * (size_t)Tn; }      // int32 [T + 1]
+  static constexpr size_t red(int Tn) { return rp(Tn) + (((size_t)4 * (Tn + 1) + 15) & ~size_t(15)); }
+  static constexpr size_t total(int Tn) { return red(Tn) + 5 * sizeof(Acc<P>) * (size_t)Tn; }
+};
+
+template <int P>
+__device__ __forceinline__ void acc_merge(Acc<P>& a, const Acc<P>& b) {
+  if constexpr (P == NSI_MIXED_F32_ACC64) {
+    a.add(b.hi);
+    a.lo += b.lo;
+  } else {
+    a.v += b.v;
+  }
+}
+
+// x / 3 of an accumulator (compensated for the pair)
+template <int P>
+__device__ __forceinline__ Acc<P> acc_third(const Acc<P>& a) {
+  Acc<P> r;
+  if constexpr (P == NSI_MIXED_F32_ACC64) {
+    const float q = a.hi * (1.0f / 3.0f);
+    r.hi = q;
+    r.lo = fmaf(a.hi, 1.0f / 3.0f, -q) + a.lo * (1.0f / 3.0f);
+  } else {
+    r.v = a.v * (typename Prec<P>::T(1) / typename Prec<P>::T(3));
+  }
+  return r;
+}
+
+// c * (a), product error kept for the pair
+template <int P>
+__device__ __forceinline__ Acc<P> acc_scale(const Acc<P>& a, typename Prec<P>::T c) {
+  Acc<P> r;
+  if constexpr (P == NSI_MIXED_F32_ACC64) {
+    const float p = c * a.hi;
+    r.hi = p;
+    r.lo = fmaf(c, a.hi, -p) + c * a.lo;
+  } else {
+    r.v = c * a.v;
+  }
+  return r;
+}
+
+template <int P, bool DEBUG>
+__device__ __forceinline__ void fan_block(const MeshView& m, const FieldView& f, const OutView& o, int64_t blk,
+                                          unsigned char* smem) {
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  constexpr int TB = FAN_BLOCK;
+  T4<T>* rec0 = reinterpret_cast<T4<T>*>(smem + FanSmem<P>::rec());
+  T4<T>* rec1 = rec0 + TB;
+  int32_t* rp = reinterpret_cast<int32_t*>(smem + FanSmem<P>::rp(TB));
+  Acc<P>* red = reinterpret_cast<Acc<P>*>(smem + FanSmem<P>::red(TB));  // 5 arrays of TB
+  const int k = threadIdx.x;
+  const int64_t R0 = m.fan_blk[blk], R1 = m.fan_blk[blk + 1];
+  const int nr = (int)(R1 - R0);
+  const int32_t base = m.row_ptr[R0];
+  const int L = m.row_ptr[R1] - base;
+  if (DEBUG && (L > TB || nr > TB)) {
+    if (k == 0) atomicOr(m.err, ERR_STAR);
+    return;
+  }
+  const T kc = kc_of<T>(f), kmu = kmu_of<T>(f), kmass = kmass_of<T>(f);
+  const T kg = (T)(-1.0 / 24.0);
+
+  // 1. row starts of the block; this entry's neighbour record (calculate_transients)
+  for (int r = k; r <= nr; r += TB) rp[r] = m.row_ptr[R0 + r] - base;
+  uint32_t w = 0;
+  if (k < L) {
+    const int j = m.col_idx[base + k];
+    w = m.fan[base + k];
+    if (!DEBUG || (j >= 0 && j < m.n)) {
+      const unsigned char* r = static_cast<const unsigned char*>(m.rec) + (size_t)j * (2 * sizeof(T4<T>));
+      if constexpr (P == NSI_FP64) {
+        cp_async16(&rec0[k], r);
+        cp_async16(reinterpret_cast<char*>(&rec0[k]) + 16, r + 16);
+        cp_async16(&rec1[k], r + 32);
+        cp_async16(reinterpret_cast<char*>(&rec1[k]) + 16, r + 48);
+      } else {
+        cp_async16(&rec0[k], r);
+        cp_async16(&rec1[k], r + 16);
+      }
+    } else {
+      atomicOr(m.err, ERR_BAD_INDEX);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // 2. this entry's row, and its edge vector from the row's own node
+  int row = 0, a = 0, len = 0, dp = 0;
+  V3<T> dj{T(0), T(0), T(0)}, uj{T(0), T(0), T(0)}, ui{T(0), T(0), T(0)};
+  if (k < L) {
+    int lo = 0, hi = nr - 1;  // last row whose start is <= k
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rp[mid] <= k) lo = mid;
+      else hi = mid - 1;
+    }
+    row = lo;
+    a = rp[row];
+    len = rp[row + 1] - a;
+    dp = m.diag_pos[R0 + row];
+    const T4<T> h = rec0[k], s = rec1[k];
+    const T4<T> hd = rec0[a + dp], sd = rec1[a + dp];
+    if constexpr (P == NSI_FP64) {
+      dj = {h.x - hd.x, h.y - hd.y, h.z - hd.z};
+      uj = {s.x, s.y, s.z};
+      ui = {sd.x, sd.y, sd.z};
+    } else {
+      const V3<float> lj = record_lo(s.z, s.w), li = record_lo(sd.z, sd.w);
+      dj = add(sub(V3<float>{h.x, h.y, h.z}, V3<float>{hd.x, hd.y, hd.z}), sub(lj, li));
+      uj = {h.w, s.x, s.y};
+      ui = {hd.w, sd.x, sd.y};
+    }
+  }
+  __syncthreads();
+  if (k < L) {
+    rec0[k] = T4<T>{dj.x, dj.y, dj.z, T(0)};
+    rec1[k] = T4<T>{uj.x, uj.y, uj.z, T(0)};
+  }
+  __syncthreads();
+
+  // 3. the fan of an off-diagonal entry, summed in registers
+  Acc<P> sA, sGx, sGy, sGz, sD;
+  sA.zero(); sGx.zero(); sGy.zero(); sGz.zero(); sD.zero();
+  const int nring = (w >> 24) & 7;
+  if (k < L && nring > 0) {
+    const bool closed = (w >> 27) & 1;
+    const int nel = closed ? nring : nring - 1;
+    const V3<T> uij{ui.x + ui.x + uj.x, ui.y + ui.y + uj.y, ui.z + ui.z + uj.z};  // 2 u_i + u_j
+    auto node = [&](int mpos, V3<T>& d, V3<T>& u) {
+      const int pos = (w >> (4 * mpos)) & 15;
+      if (DEBUG && pos >= len) atomicOr(m.err, ERR_STAR);
+      const T4<T> x = rec0[a + pos], y = rec1[a + pos];
+      d = {x.x, x.y, x.z};
+      u = {y.x, y.y, y.z};
+    };
+    V3<T> d0, u0;
+    node(0, d0, u0);
+    V3<T> q0 = cross(dj, d0);
+    const V3<T> dfirst = d0, ufirst = u0, qfirst = q0;
+    for (int e = 0; e < nel; ++e) {
+      V3<T> d1, u1, q1;
+      if (e + 1 < nring) {
+        node(e + 1, d1, u1);
+        q1 = cross(dj, d1);
+      } else {  // closing element of an interior ring
+        d1 = dfirst;
+        u1 = ufirst;
+        q1 = qfirst;
+      }
+      const V3<T> cj = cross(d0, d1);
+      const T det = dot(dj, cj);
+      const V3<T> ci{-(cj.x + q0.x - q1.x), -(cj.y + q0.y - q1.y), -(cj.z + q0.z - q1.z)};
+      const T kv = kmu * rcp_fast(det);
+      const V3<T> w3{kc * (uij.x + u0.x + u1.x) + kv * ci.x, kc * (uij.y + u0.y + u1.y) + kv * ci.y,
+                     kc * (uij.z + u0.z + u1.z) + kv * ci.z};
+      sA.add(dot(w3, cj));
+      sGx.add(ci.x);
+      sGy.add(ci.y);
+      sGz.add(ci.z);
+      sD.add(det);
+      d0 = d1;
+      u0 = u1;
+      q0 = q1;
+    }
+  }
+
+  // 4. row totals for the diagonal: tree reduction over each row's entries
+  Acc<P>* rA = red;
+  Acc<P>* rGx = red + TB;
+  Acc<P>* rGy = red + 2 * TB;
+  Acc<P>* rGz = red + 3 * TB;
+  Acc<P>* rD = red + 4 * TB;
+  if (k < L) {
+    rA[k] = sA;
+    rGx[k] = sGx;
+    rGy[k] = sGy;
+    rGz[k] = sGz;
+    rD[k] = sD;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int st = 1; st < FAN_MAX_ROW; st <<= 1) {
+    if (k < L && ((k - a) & (2 * st - 1)) == 0 && k - a + st < len) {
+      acc_merge<P>(rA[k], rA[k + st]);
+      acc_merge<P>(rGx[k], rGx[k + st]);
+      acc_merge<P>(rGy[k], rGy[k + st]);
+      acc_merge<P>(rGz[k], rGz[k + st]);
+      acc_merge<P>(rD[k], rD[k + st]);
+    }
+    __syncthreads();
+  }
+
+  // 5. this entry's outputs (coalesced across the block), the diagonal's and the RHS
+  Out* A = static_cast<Out*>(o.A);
+  Out* G = static_cast<Out*>(o.G);
+  Out* Rh = static_cast<Out*>(o.rhs);
+  if (k < L) {
+    const int64_t g = (int64_t)base + k;
+    if (k == a + dp) {
+      const Acc<P> d3 = acc_third<P>(rD[a]);
+      const Acc<P> mass = acc_scale<P>(d3, kmass);
+      Acc<P> add_ = mass;
+      if constexpr (P == NSI_MIXED_F32_ACC64) {
+        add_.add(-rA[a].hi);
+        add_.lo -= rA[a].lo;
+      } else {
+        add_.v = mass.v - rA[a].v;
+      }
+      store_acc(A + g, add_);
+      store_acc(G + g, acc_scale<P>(acc_third<P>(rGx[a]), kg));
+      store_acc(G + m.nnz + g, acc_scale<P>(acc_third<P>(rGy[a]), kg));
+      store_acc(G + 2 * m.nnz + g, acc_scale<P>(acc_third<P>(rGz[a]), kg));
+      const int64_t i = R0 + row;
+      const V3<T> un = load_vec<T>(f.un, i);
+      store_acc(Rh + i, acc_scale<P>(mass, un.x));
+      store_acc(Rh + m.n + i, acc_scale<P>(mass, un.y));
+      store_acc(Rh + 2 * m.n + i, acc_scale<P>(mass, un.z));
+    } else {
+      store_acc(A + g, sA);
+      store_acc(G + g, acc_scale<P>(sGx, kg));
+      store_acc(G + m.nnz + g, acc_scale<P>(sGy, kg));
+      store_acc(G + 2 * m.nnz + g, acc_scale<P>(sGz, kg));
+    }
+  }
+  // rows without entries (nodes in no element): zero right-hand side
+  for (int r = k; r < nr; r += TB) {
+    if (rp[r + 1] == rp[r]) {
+      Acc<P> z;
+      z.zero();
+      store_acc(Rh + R0 + r, z);
+      store_acc(Rh + m.n + R0 + r, z);
+      store_acc(Rh + 2 * m.n + R0 + r, z);
+    }
+  }
+}
+
+template <int P, bool DEBUG>
+__global__ void __launch_bounds__(FAN_BLOCK) fan_kernel(MeshView m, FieldView f, OutView o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fan_block<P, DEBUG>(m, f, o, blockIdx.x, smem_raw);
+}
+
 template <int P, bool DEBUG>
 __global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, OutView o, GatherSmem lay) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -859,6 +1130,24 @@ __global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ Ba
     }
     const BatchItem& it = args.item[lo];
     gather_rows<P, false>(it.m, it.f, it.o, (b - it.block0) * blockDim.x, smem_raw, lay);
+    __syncthreads();  // the next block reuses the shared records
+  }
+}
+
+// many meshes, edge-fan variant: a persistent grid strides over the fan
+// blocks of all meshes (item.block0 counts fan blocks here)
+template <int P>
+__global__ void __launch_bounds__(FAN_BLOCK) batched_fan_kernel(const __grid_constant__ BatchArgs args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int64_t b = blockIdx.x; b < args.total_blocks; b += gridDim.x) {
+    int lo = 0, hi = args.count - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (args.item[mid].block0 <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchItem& it = args.item[lo];
+    fan_block<P, false>(it.m, it.f, it.o, b - it.block0, smem_raw);
     __syncthreads();  // the next block reuses the shared records
   }
 }
@@ -1067,6 +1356,14 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
   if (st) return st;
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, h->rec);
+  if (h->use_fan) {
+    const size_t fsm = FanSmem<P>::total(FAN_BLOCK);
+    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
+    if (h->debug) fan_kernel<P, true><<<h->fan_blocks, FAN_BLOCK, fsm, s>>>(m, f, o);
+    else fan_kernel<P, false><<<h->fan_blocks, FAN_BLOCK, fsm, s>>>(m, f, o);
+    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
+    return check_launch("fan_kernel");
+  }
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
   const size_t smem = lay.total();
@@ -1117,6 +1414,30 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   args.count = count;
+  bool all_fan = true;
+  for (int k = 0; k < count; ++k) all_fan &= hs[k]->use_fan;
+  if (all_fan) {
+    int64_t fblocks = 0;
+    for (int k = 0; k < count; ++k) {
+      args.item[k].m = view_of(hs[k]);
+      args.item[k].f = fields_of(&fs[k]);
+      args.item[k].o = OutView{os[k].A_val, os[k].G_val, os[k].rhs};
+      args.item[k].block0 = fblocks;
+      fblocks += hs[k]->fan_blocks;
+    }
+    args.total_blocks = fblocks;
+    if (fblocks == 0) return NSI_OK;
+    for (int k = 0; k < count; ++k)
+      pack_kernel<P><<<(hs[k]->n + 255) / 256, 256, 0, s>>>(args.item[k].m, args.item[k].f, hs[k]->rec);
+    const size_t fsm = FanSmem<P>::total(FAN_BLOCK);
+    int per_sm = 0, sms = 0, dev = 0;
+    NSI_CUDA(cudaGetDevice(&dev));
+    NSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    NSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fan_kernel<P>, FAN_BLOCK, fsm));
+    const int64_t grid = std::min<int64_t>(fblocks, (int64_t)std::max(1, per_sm) * sms);
+    batched_fan_kernel<P><<<grid, FAN_BLOCK, fsm, s>>>(args);
+    return check_launch("batched_fan_kernel");
+  }
   // one block size for the whole batch: the smallest planned one.  A mesh's
   // per-block maxima, taken over blocks of its own (larger or equal) size,
   // bound its blocks of the smaller size too.
@@ -1217,6 +1538,10 @@ static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const Out
   MeshView m = view_of(h);
   m.rec = scratch;
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, scratch);
+  if (h->use_fan) {
+    fan_kernel<P, false><<<h->fan_blocks, FAN_BLOCK, FanSmem<P>::total(FAN_BLOCK), s>>>(m, f, o);
+    return check_launch("fan_kernel (no-alloc)");
+  }
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
   gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay);
@@ -1321,19 +1646,22 @@ nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, i
   NSI_CUDA(cudaEventCreate(&e0));
   NSI_CUDA(cudaEventCreate(&e1));
   struct Cand {
-    int scatter, plan;
+    int scatter, plan;  // plan: index into h->plans (star kernel), -2: edge-fan kernel, -1: n/a
   };
   std::vector<Cand> cands;
+  if (h->fan_ok) cands.push_back({NSI_SCATTER_GATHER, -2});
   if (h->gather_ok)
     for (int k = 0; k < h->n_plans; ++k) cands.push_back({NSI_SCATTER_GATHER, k});
   cands.push_back({NSI_SCATTER_COLOR, -1});
   cands.push_back({NSI_SCATTER_ATOMIC, -1});
   const GatherPlan saved = h->plan;
+  const bool saved_fan = h->use_fan;
   float best = 1e30f;
-  Cand pick{h->scatter, -1};
+  Cand pick{h->scatter, saved_fan ? -2 : -1};
   cudaEvent_t ev0 = h->ev_start, ev1 = h->ev_stop;
   h->ev_start = h->ev_stop = nullptr;
   for (const Cand& c : cands) {
+    h->use_fan = c.plan == -2;
     if (c.plan >= 0) h->plan = h->plans[c.plan];
     st = assemble_dispatch(h, f, o, c.scatter, s);  // warm-up
     if (st) break;
@@ -1358,10 +1686,12 @@ nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, i
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->plan = pick.plan >= 0 ? h->plans[pick.plan] : saved;
+  h->use_fan = pick.plan == -2 || (pick.plan == -1 && saved_fan);
   if (st) return st;
   h->scatter = pick.scatter;
   if (chosen_scatter) *chosen_scatter = pick.scatter;
-  if (chosen_rows) *chosen_rows = pick.scatter == NSI_SCATTER_GATHER ? h->plan.rows_per_block : 0;
+  if (chosen_rows)
+    *chosen_rows = pick.scatter != NSI_SCATTER_GATHER ? 0 : (h->use_fan ? -1 : h->plan.rows_per_block);
   return NSI_OK;
 }
 

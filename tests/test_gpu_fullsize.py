@@ -173,7 +173,7 @@ def test_autotune_choice_and_cache(tmp_path):
     sc, rows = asm.autotune(ut, cache=cache, reps=3)
     assert sc in ("gather", "color", "atomic")
     if sc == "gather":
-        assert rows in (32, 64, 96, 128)
+        assert rows in (-1, 32, 64, 96, 128)
     out = asm.assemble(ut)
     torch.cuda.synchronize()
     for a, b in zip(out, ref):

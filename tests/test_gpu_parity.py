@@ -111,6 +111,23 @@ def test_single_tet_and_isolated_node():
             assert max(err.values()) <= TOL[precision], (precision, scatter, err)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_edge_fan_kernel_matches_oracle(precision):
+    """The edge-fan variant of the row gather (selected with nsi_set_launch(-1))."""
+    for kw in (dict(N=7, jitter=0.15, numbering="random", seed=71), dict(name="cube8")):
+        mesh, u = meshgen.config_mesh(**kw) if "name" not in kw else meshgen.config_mesh(kw["name"])
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter="gather")
+        nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
+        assert asm.info().rows_per_block == -1
+        A, G, rhs = asm.assemble(torch.as_tensor(u.T.copy()))
+        rp, ci = asm.pattern()
+        _, _, oA, oG, orhs = _oracle(mesh, u, precision)
+        err = errors(rp.cpu().numpy(), A.double().cpu().numpy(), G.double().cpu().numpy(),
+                     rhs.double().cpu().numpy(), oA, oG, orhs)
+        assert max(err.values()) <= TOL[precision], err
+        asm.close()
+
+
 def test_ragged_row_blocks():
     """n not a multiple of the rows-per-block and rows of uneven length (boundary)."""
     mesh, u = meshgen.config_mesh(N=11, jitter=0.15, numbering="random", seed=43)
