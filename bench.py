@@ -285,6 +285,8 @@ def run_gpu(args, world, rank, local):
     precs = [main_prec] + ([p for p in ("fp64", "mixed32", "mixed64") if p != main_prec] if not args.quick else [])
     for prec in precs:
         asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec, scatter=args.scatter)
+        if args.fan:
+            nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
         vt = torch.float64 if prec == "fp64" else torch.float32
         ut = torch.as_tensor(u.T.copy()).to(dev, vt).contiguous()
         out = asm.empty_outputs()
@@ -345,7 +347,8 @@ def run_gpu(args, world, rank, local):
     main = results[main_prec]
     ms_max = allreduce_max(main["ms"], world)
     value = world * E / (ms_max * 1e-3)
-    kernel = {"gather": "gather_kernel", "atomic": "elem_kernel", "color": "elem_kernel"}[main["mode"]]
+    kernel = {"gather": "fan_kernel" if args.fan else "gather_kernel", "atomic": "elem_kernel",
+              "color": "elem_kernel"}[main["mode"]]
     bytes_alg = algorithmic_bytes(E, n, main["nnz"], main_prec)
     peaks = {}
     try:
@@ -496,6 +499,8 @@ def run_profile(args):
     mesh, u = meshgen.config_mesh(args.workload)
     for prec in args.profile_run.split(","):
         asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec, scatter=args.scatter)
+        if args.fan:
+            nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
         vt = torch.float64 if prec == "fp64" else torch.float32
         ut = torch.as_tensor(u.T.copy()).cuda().to(vt)
         out = asm.empty_outputs()
@@ -521,6 +526,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="time only the main precision")
     ap.add_argument("--autotune", action="store_true", help="batch64: autotune launch shapes (cached)")
+    ap.add_argument("--fan", action="store_true", help="row gather through the edge-fan kernel")
     ap.add_argument("--profile-run", default=None, metavar="PRECS",
                     help="no timing: 3 assembly calls per listed precision (for ncu)")
     args = ap.parse_args()
