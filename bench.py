@@ -142,7 +142,7 @@ class ClockSampler:
         return out
 
 
-def dist_setup():
+def dist_setup(cpu_only=False):
     import torch
     import torch.distributed as dist
 
@@ -150,10 +150,10 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if torch.cuda.is_available():
+        gpu = torch.cuda.is_available() and not cpu_only
+        if gpu:
             torch.cuda.set_device(local)
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if gpu else "gloo")
     return world, rank, local
 
 
@@ -170,7 +170,8 @@ def allreduce_max(x, world):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    on_gpu = torch.cuda.is_available() and dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -534,7 +535,7 @@ def main():
     if args.profile_run:
         run_profile(args)
         return
-    world, rank, local = dist_setup()
+    world, rank, local = dist_setup(cpu_only=args.impl == "reference")
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
