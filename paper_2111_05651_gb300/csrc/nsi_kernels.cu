@@ -461,6 +461,29 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     hi[k] = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
     lo[k] = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
   }
+  // convert slot k in place: the slot's 32 bytes become the four finished
+  // doubles (A, G_x in the hi half; G_y, G_z in the lo half)
+  __device__ __forceinline__ void finalize_inplace(int k, float kg) {
+    const float4 h4 = hi[k], l4 = lo[k];
+    Acc<NSI_MIXED_F32_ACC64> t;
+    double r[4];
+    t.hi = h4.x;
+    t.lo = l4.x;
+    store_acc(&r[0], t);
+    const float hv[3] = {h4.y, h4.z, h4.w}, lv[3] = {l4.y, l4.z, l4.w};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {  // kg * (hi + lo), keeping the product error of the leading part
+      const float p = kg * hv[c];
+      t.hi = p;
+      t.lo = fmaf(kg, hv[c], -p) + kg * lv[c];
+      store_acc(&r[c + 1], t);
+    }
+    reinterpret_cast<double2*>(hi)[k] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2*>(lo)[k] = make_double2(r[2], r[3]);
+  }
+  __device__ __forceinline__ double2 finished(int k, int half) const {
+    return reinterpret_cast<const double2*>(half ? lo : hi)[k];
+  }
   template <int C>
   __device__ __forceinline__ double value(int k, float kg) const {
     const float4 h4 = hi[k], l4 = lo[k];
@@ -789,6 +812,7 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   if constexpr (sizeof(Out) == sizeof(T4<T>) / 4 || P == NSI_FP64) {
     // room for all four components at once
     if (t < nrows) {
+#pragma unroll 4
       for (int q = 0, k = t; q < len; ++q, k += R) {
         stage[lb + q] = acc.template value<0>(k, kg);
         stage[L + lb + q] = acc.template value<1>(k, kg);
@@ -804,29 +828,28 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
       dst[3][k] = stage[3 * L + k];
     }
   } else {
-    // double values out of float slots: two components per round
+    // double values out of compensated float slots: every thread converts its
+    // own slots in place once, then two components per staging round
     if (t < nrows) {
-      for (int q = 0, k = t; q < len; ++q, k += R) {
-        stage[lb + q] = acc.template value<0>(k, kg);
-        stage[L + lb + q] = acc.template value<1>(k, kg);
+#pragma unroll 4
+      for (int q = 0; q < len; ++q) acc.finalize_inplace(q * R + t, kg);
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      if (t < nrows) {
+#pragma unroll 4
+        for (int q = 0; q < len; ++q) {
+          const double2 v = acc.finished(q * R + t, half);
+          stage[lb + q] = v.x;
+          stage[L + lb + q] = v.y;
+        }
       }
-    }
-    __syncthreads();
-    for (int k = t; k < L; k += R) {
-      dst[0][k] = stage[k];
-      dst[1][k] = stage[L + k];
-    }
-    __syncthreads();
-    if (t < nrows) {
-      for (int q = 0, k = t; q < len; ++q, k += R) {
-        stage[lb + q] = acc.template value<2>(k, kg);
-        stage[L + lb + q] = acc.template value<3>(k, kg);
+      __syncthreads();
+      for (int k = t; k < L; k += R) {
+        dst[2 * half][k] = stage[k];
+        dst[2 * half + 1][k] = stage[L + k];
       }
-    }
-    __syncthreads();
-    for (int k = t; k < L; k += R) {
-      dst[2][k] = stage[k];
-      dst[3][k] = stage[L + k];
+      if (half == 0) __syncthreads();
     }
   }
 }
