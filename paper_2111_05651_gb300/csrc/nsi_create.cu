@@ -63,8 +63,8 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->col_idx);
   cudaFree(h->lnods);
   cudaFree(h->color_elems);
-  cudaFree(h->star_ptr);
-  cudaFree(h->star);
+  cudaFree(h->walk_ptr);
+  cudaFree(h->walk);
   cudaFree(h->diag_pos);
   cudaFree(h->fan);
   cudaFree(h->fan_blk);
@@ -78,6 +78,202 @@ static void free_handle(NsiHandle* h) {
 }
 
 // Mesh preparation ---------------------------------------------------------
+// The element walk of one row: the order in which the row-gather kernel visits
+// the elements of the star of node i, and the one-byte steps that drive it.
+// Every element of the star is a triangle of row positions (the face opposite
+// i, listed so that (i, a, b, c) has the element's orientation).  Two
+// triangles that share two positions are neighbours; the walk follows paths of
+// that neighbour graph, so consecutive elements share an edge and each step
+// brings one new node into a window of two (the kernel keeps the window in
+// registers and reads one node's data per element instead of three).  A path
+// starts with two steps that only fill the window; a later path first flushes
+// the window with two steps on the diagonal position dp, whose slot stays
+// zero until the kernel writes the diagonal.  The kernel prefetches the next
+// step's node while the current element is evaluated, so a step never brings
+// in a node held by the previous step (dp excepted); the encoder checks this.
+struct WalkWork {  // per-thread buffers of encode_walk
+  std::vector<std::pair<int, int>> ed;
+  std::vector<int> adj, nadj, cand, ncand, idx, path, best;
+  std::vector<char> used;
+};
+
+static bool encode_walk(const uint16_t* tri, int m, int dp, std::vector<uint8_t>& out, WalkWork& ws) {
+  constexpr int MAXN = 8;  // neighbours kept per triangle (3 in a manifold link)
+  auto P = [&](int t, int c) { return (int)((tri[t] >> (STAR_BITS * c)) & (STAR_MAX_ROW - 1)); };
+  auto has = [&](int t, int v) { return P(t, 0) == v || P(t, 1) == v || P(t, 2) == v; };
+  // (a, b) consecutive in t's cyclic order: (a, b, third) is an even permutation
+  auto even = [&](int t, int a, int b) {
+    for (int c = 0; c < 3; ++c)
+      if (P(t, c) == a && P(t, (c + 1) % 3) == b) return true;
+    return false;
+  };
+  // neighbours through shared edges (sorted edge records)
+  auto& ed = ws.ed;
+  ed.clear();
+  for (int t = 0; t < m; ++t)
+    for (int c = 0; c < 3; ++c) {
+      const int a = P(t, c), b = P(t, (c + 1) % 3);
+      ed.push_back({std::min(a, b) * STAR_MAX_ROW + std::max(a, b), t});
+    }
+  std::sort(ed.begin(), ed.end());
+  ws.adj.assign((size_t)m * MAXN, -1);
+  ws.nadj.assign(m, 0);
+  for (size_t x = 0; x < ed.size();) {
+    size_t y = x;
+    while (y < ed.size() && ed[y].first == ed[x].first) ++y;
+    for (size_t a = x; a < y; ++a)
+      for (size_t b = x; b < y; ++b) {
+        const int ta = ed[a].second, tb = ed[b].second;
+        if (ta == tb || ws.nadj[ta] == MAXN) continue;
+        bool dup = false;
+        for (int k = 0; k < ws.nadj[ta]; ++k) dup |= ws.adj[ta * MAXN + k] == tb;
+        if (!dup) ws.adj[ta * MAXN + ws.nadj[ta]++] = tb;
+      }
+    x = y;
+  }
+  // path cover: depth-first search for a long path, neighbours with the fewest
+  // unvisited neighbours first, with bounded work per path
+  auto& used = ws.used;  // 0 free, 1 emitted, 2 on the current path
+  used.assign(m, 0);
+  auto deg = [&](int t) {
+    int d = 0;
+    for (int k = 0; k < ws.nadj[t]; ++k) d += used[ws.adj[t * MAXN + k]] == 0;
+    return d;
+  };
+  auto by_deg = [&](int* a, int n) {  // insertion sort, n <= MAXN
+    for (int x = 1; x < n; ++x)
+      for (int y = x; y > 0 && deg(a[y]) < deg(a[y - 1]); --y) std::swap(a[y], a[y - 1]);
+  };
+  ws.cand.assign((size_t)m * MAXN, 0);
+  ws.ncand.assign(m, 0);
+  ws.idx.assign(m, 0);
+  std::vector<std::vector<int>> paths;
+  int left = m;
+  while (left > 0) {
+    auto& best = ws.best;
+    auto& path = ws.path;
+    best.clear();
+    int starts[3], nst = 0;
+    {  // up to three free triangles with the fewest free neighbours
+      int dbest[3];
+      for (int t = 0; t < m; ++t) {
+        if (used[t]) continue;
+        const int d = deg(t);
+        int x = nst < 3 ? nst++ : 3;
+        while (x > 0 && dbest[x - 1] > d) {
+          if (x < 3) {
+            starts[x] = starts[x - 1];
+            dbest[x] = dbest[x - 1];
+          }
+          --x;
+        }
+        if (x < 3) {
+          starts[x] = t;
+          dbest[x] = d;
+        }
+      }
+    }
+    int work = 0;
+    const int budget = 64 * m + 256;
+    for (int k = 0; k < nst && (int)best.size() < left; ++k) {
+      path.assign(1, starts[k]);
+      used[starts[k]] = 2;
+      ws.idx[0] = -1;  // candidates of this depth not listed yet
+      while (!path.empty()) {
+        if (path.size() > best.size()) best = path;
+        if ((int)best.size() == left || work > budget) break;
+        const int d = (int)path.size() - 1;
+        int* cd = &ws.cand[(size_t)d * MAXN];
+        if (ws.idx[d] < 0) {
+          const int t = path[d];
+          int nc = 0;
+          for (int a = 0; a < ws.nadj[t]; ++a)
+            if (!used[ws.adj[t * MAXN + a]]) cd[nc++] = ws.adj[t * MAXN + a];
+          by_deg(cd, nc);
+          ws.ncand[d] = nc;
+          ws.idx[d] = 0;
+        }
+        if (ws.idx[d] < ws.ncand[d]) {
+          const int u = cd[ws.idx[d]++];
+          if (used[u]) continue;
+          ++work;
+          used[u] = 2;
+          path.push_back(u);
+          ws.idx[d + 1] = -1;
+        } else {
+          used[path.back()] = 0;
+          path.pop_back();
+        }
+      }
+      for (int t : path) used[t] = 0;
+    }
+    for (int t : best) used[t] = 1;
+    left -= (int)best.size();
+    paths.push_back(best);
+  }
+  // emission, simulating the kernel's window (wp, wq) and the nodes held by
+  // the previous step (r0, r1, r2)
+  int wp = dp, wq = dp, r0 = dp, r1 = dp, r2 = dp;
+  auto emit = [&](int c, bool elem, bool neg, bool evq) {
+    if (c != dp && (c == r0 || c == r1 || c == r2)) return false;
+    out.push_back((uint8_t)(c | (elem ? WALK_ELEM : 0u) | (neg ? WALK_NEG : 0u) | (evq ? WALK_EVQ : 0u)));
+    r0 = wp;
+    r1 = wq;
+    r2 = c;
+    if (evq) {
+      wq = wp;
+      wp = c;
+    } else {
+      wp = wq;
+      wq = c;
+    }
+    return true;
+  };
+  for (size_t pi = 0; pi < paths.size(); ++pi) {
+    std::vector<int> path = paths[pi];
+    if (pi > 0) {
+      emit(dp, false, false, false);
+      emit(dp, false, false, false);
+    }
+    // first element (x, y, z) in its own order, z on the edge shared with the
+    // next element; x must not be a node the flush still holds
+    const int t0 = path[0];
+    int x = -1, y = -1, z = -1;
+    for (int c = 0; c < 3 && x < 0; ++c) {
+      const int zc = P(t0, c);
+      if (path.size() > 1 && !has(path[1], zc)) continue;
+      const int xc = P(t0, (c + 1) % 3);
+      if (xc != dp && (xc == r0 || xc == r1 || xc == r2)) continue;
+      x = xc;
+      y = P(t0, (c + 2) % 3);
+      z = zc;
+    }
+    if (x < 0 || !emit(x, false, false, false) || !emit(y, false, false, false)) return false;
+    for (size_t k = 0; k < path.size(); ++k) {
+      const int t = path[k];
+      if (!has(t, wp) || !has(t, wq)) return false;
+      const int c = k == 0 ? z : P(t, 0) ^ P(t, 1) ^ P(t, 2) ^ wp ^ wq;
+      bool evq = false;
+      bool split = false;
+      if (k + 1 < path.size()) {
+        const int nx = path[k + 1];
+        if (has(nx, c) && has(nx, wq))
+          evq = false;
+        else if (has(nx, c) && has(nx, wp))
+          evq = true;
+        else
+          split = true;  // the next element shares the window's own edge
+      }
+      if (!emit(c, true, !even(t, wp, wq), evq)) return false;
+      if (split) {
+        paths.push_back(std::vector<int>(path.begin() + k + 1, path.end()));
+        break;
+      }
+    }
+  }
+  return true;
+}
+
 static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   const int64_t n = h->n, E = h->E;
   std::vector<int32_t> ln(4 * E);
@@ -167,12 +363,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
 
   // 4. row-gather map (positions of the other three nodes in the row)
   h->gather_ok = max_row <= STAR_MAX_ROW;
-  std::vector<int32_t> star_ptr(n + 1, 0);
   std::vector<uint16_t> star;
   std::vector<uint8_t> diag(n, 0);
   if (h->gather_ok) {
     if (inc_ptr[n] > INT32_MAX) return fail(NSI_ERR_UNSUPPORTED, "too many element-node incidences");
-    for (int64_t i = 0; i <= n; ++i) star_ptr[i] = (int32_t)inc_ptr[i];
     star.resize(inc_ptr[n]);
     // even permutations of (0,1,2,3) that bring vertex a to the front
     static const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
@@ -191,6 +385,42 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
         }
       }
     });
+  }
+
+  // 4a. every row's element walk (the order and steps of the kernel's element loop)
+  std::vector<int32_t> walk_ptr;
+  std::vector<uint8_t> walk;
+  if (h->gather_ok) {
+    std::vector<int32_t> wlen(n, 0);
+    std::vector<std::pair<int64_t, std::vector<uint8_t>>> parts;
+    std::mutex mu;
+    std::atomic<bool> bad{false};
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+      std::vector<uint8_t> buf;
+      WalkWork ws;
+      for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); ++i) {
+        const size_t before = buf.size();
+        if (!encode_walk(&star[inc_ptr[i]], (int)(inc_ptr[i + 1] - inc_ptr[i]), diag[i], buf, ws)) bad = true;
+        wlen[i] = (int32_t)(buf.size() - before);
+      }
+      std::lock_guard<std::mutex> g(mu);
+      parts.emplace_back(lo, std::move(buf));
+    });
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) total += wlen[i];
+    if (bad.load() || total > INT32_MAX - 64) {
+      h->gather_ok = false;
+    } else {
+      walk_ptr.assign(n + 1, 0);
+      for (int64_t i = 0; i < n; ++i) walk_ptr[i + 1] = walk_ptr[i] + wlen[i];
+      std::sort(parts.begin(), parts.end(),
+                [](const std::pair<int64_t, std::vector<uint8_t>>& a, const std::pair<int64_t, std::vector<uint8_t>>& b) {
+                  return a.first < b.first;
+                });
+      walk.reserve(total + 8);
+      for (auto& pr : parts) walk.insert(walk.end(), pr.second.begin(), pr.second.end());
+      walk.resize(total + 8, 0);  // the kernel copies whole aligned words
+    }
   }
 
   // 4b. edge-fan map: per off-diagonal entry (i, j) the ring of nodes around the edge
@@ -336,11 +566,12 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     const int W = std::max(1, (int)max_row);
     int chosen = 0, chosen_L = 0, chosen_S = 0, best_warps = 0;
     for (int R : {128, 96, 64, 32}) {
+      if (!h->gather_ok) break;
       int64_t mL = 0, mS = 0;
       for (int64_t r0 = 0; r0 < n; r0 += R) {
         const int64_t r1 = std::min(n, r0 + R);
         mL = std::max<int64_t>(mL, rp64[r1] - rp64[r0]);
-        mS = std::max<int64_t>(mS, inc_ptr[r1] - inc_ptr[r0]);
+        mS = std::max<int64_t>(mS, walk_ptr[r1] - walk_ptr[r0]);
       }
       const size_t sm = gather_smem(h->precision, R, W, (int)mL, (int)mS).total();
       if (sm > smem_max) continue;
@@ -350,7 +581,7 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
       GatherPlan cand;
       cand.rows_per_block = R;
       cand.max_block_entries = (int)mL;
-      cand.max_block_stars = (int)mS;
+      cand.max_block_steps = (int)mS;
       cand.n_blocks = (n + R - 1) / R;
       h->plans[h->n_plans++] = cand;
       if (warps > best_warps) {
@@ -363,7 +594,7 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if (chosen == 0) h->gather_ok = false;
     h->plan.rows_per_block = chosen;
     h->plan.max_block_entries = chosen_L;
-    h->plan.max_block_stars = chosen_S;
+    h->plan.max_block_steps = chosen_S;
     h->plan.n_blocks = chosen ? (n + chosen - 1) / chosen : 0;
   }
 
@@ -381,8 +612,8 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->fan_blk, fan_blk.data(), fan_blk.size(), s))) return st;
   }
   if (h->gather_ok) {
-    if ((st = dev_upload(h, &h->star_ptr, star_ptr.data(), n + 1, s))) return st;
-    if ((st = dev_upload(h, &h->star, star.data(), star.size(), s))) return st;
+    if ((st = dev_upload(h, &h->walk_ptr, walk_ptr.data(), n + 1, s))) return st;
+    if ((st = dev_upload(h, &h->walk, walk.data(), walk.size(), s))) return st;
     if ((st = dev_upload(h, &h->diag_pos, diag.data(), n, s))) return st;
   }
   if (h->precision == NSI_FP64) {

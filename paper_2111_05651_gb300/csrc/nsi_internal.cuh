@@ -35,6 +35,14 @@ enum : unsigned { ERR_BAD_INDEX = 1u, ERR_NOT_IN_PATTERN = 2u, ERR_STAR = 4u };
 // encoded; such meshes do not support the gather mode.
 constexpr int STAR_BITS = 5;
 constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
+// One step of a row's element walk (one byte): the row position of the node
+// it brings into the window, whether the element formed by the window and that
+// node is evaluated, the element's orientation in window order, and which
+// window node leaves afterwards.
+constexpr unsigned WALK_POS = 31u;       // bits 0-4: row position of the new node
+constexpr unsigned WALK_ELEM = 1u << 5;  // the step evaluates element (p, q, c)
+constexpr unsigned WALK_NEG = 1u << 6;   // (p, q, c) is an odd permutation of the element's order
+constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves (window becomes (c, p)); else p leaves (window (q, c))
 
 // Edge-fan map: for every off-diagonal CSR entry (i, j), the ring of nodes
 // around the edge (i, j) -- the other two nodes of every element containing
@@ -58,20 +66,20 @@ struct alignas(32) D4 {
 struct GatherPlan {
   int rows_per_block = 0;     // threads per block = rows per block
   int max_block_entries = 0;  // max over blocks of the CSR entries of the block's rows
-  int max_block_stars = 0;    // max over blocks of the row-gather words of the block's rows
+  int max_block_steps = 0;    // max over blocks of the walk steps of the block's rows
   int64_t n_blocks = 0;
 };
 
 // Shared-memory layout of one row-gather block: R rows (one per thread), W
-// slots per row (the longest row of the mesh), L CSR entries and S row-gather
-// words.  Slot q of row t lives at index q * R + t ("thread-interleaved"), so
+// slots per row (the longest row of the mesh), L CSR entries and S walk
+// steps.  Slot q of row t lives at index q * R + t ("thread-interleaved"), so
 // the lanes of a warp touch consecutive records whichever slot each lane
 // uses: the element loop is free of shared-memory bank conflicts.
 //   nb0   T[4] per slot: edge vector d = x_j - x_i and u_x of the neighbour
 //   nb1   T[2] per slot: u_y, u_z
 //   acc   accumulators per slot (ab bytes): A and the three sums of c_i
-//   col   int32 per CSR entry; star uint16 per word (copied as aligned pairs,
-//         so S + 2 of them)
+//   col   int32 per CSR entry; walk one byte per step (copied as aligned
+//         4-byte words, so S + 8 bytes)
 // After the element loop, nb0 is reused to stage the finished values in CSR
 // order for the coalesced write-out.
 // Used identically by the host (launch size) and the kernel (carving).
@@ -83,8 +91,8 @@ struct GatherSmem {
   __host__ __device__ size_t nb1() const { return up16(nb0() + (size_t)4 * tb * N()); }
   __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
   __host__ __device__ size_t col() const { return up16(acc() + (size_t)ab * N()); }
-  __host__ __device__ size_t star() const { return up16(col() + (size_t)4 * L); }
-  __host__ __device__ size_t total() const { return up16(star() + (size_t)2 * (S + 2)); }
+  __host__ __device__ size_t walk() const { return up16(col() + (size_t)4 * L); }
+  __host__ __device__ size_t total() const { return up16(walk() + (size_t)S + 8); }
 };
 
 __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S) {
@@ -121,9 +129,9 @@ struct NsiHandle {
   int4* lnods = nullptr;        // [E]
   int32_t* color_elems = nullptr;  // [E] element ids grouped by colour
   std::vector<int64_t> color_off;  // host [n_colors + 1]
-  // row-gather map
-  int32_t* star_ptr = nullptr;  // [n+1]
-  uint16_t* star = nullptr;     // [star_ptr[n]]
+  // row-gather map: every row's element walk (one byte per step)
+  int32_t* walk_ptr = nullptr;  // [n+1]
+  uint8_t* walk = nullptr;      // [walk_ptr[n] + 8]
   uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row
   // edge-fan map (one word per CSR entry) and its block partition of the rows
   bool fan_ok = false;

@@ -28,8 +28,8 @@ struct MeshView {
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col_idx;
   const int4* __restrict__ lnods;
-  const int32_t* __restrict__ star_ptr;
-  const uint16_t* __restrict__ star;
+  const int32_t* __restrict__ walk_ptr;
+  const uint8_t* __restrict__ walk;
   const uint8_t* __restrict__ diag_pos;
   const D4* __restrict__ xyz64;
   const float4* __restrict__ xyz_hi;
@@ -80,8 +80,8 @@ static MeshView view_of(const NsiHandle* h) {
   m.row_ptr = h->row_ptr;
   m.col_idx = h->col_idx;
   m.lnods = h->lnods;
-  m.star_ptr = h->star_ptr;
-  m.star = h->star;
+  m.walk_ptr = h->walk_ptr;
+  m.walk = h->walk;
   m.diag_pos = h->diag_pos;
   m.xyz64 = h->xyz64;
   m.xyz_hi = h->xyz_hi;
@@ -374,20 +374,14 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
   float4* __restrict__ a;
   __device__ __forceinline__ AccSmem(unsigned char* p, size_t) : a(reinterpret_cast<float4*>(p)) {}
   __device__ __forceinline__ void zero(int k) { a[k] = make_float4(0.f, 0.f, 0.f, 0.f); }
-  struct Slots {
-    float4 v1, v2, v3;
-  };
-  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const { return {a[k1], a[k2], a[k3]}; }
-  static __device__ __forceinline__ void update(Slots& s, float A1, float A2, float A3, float gx, float gy,
-                                                float gz) {
-    s.v1.x += A1; s.v1.y += gx; s.v1.z += gy; s.v1.w += gz;
-    s.v2.x += A2; s.v2.y += gx; s.v2.z += gy; s.v2.w += gz;
-    s.v3.x += A3; s.v3.y += gx; s.v3.z += gy; s.v3.w += gz;
+  using Slot = float4;  // A, sum c_i x, sum c_i y, sum c_i z
+  __device__ __forceinline__ Slot load1(int k) const { return a[k]; }
+  __device__ __forceinline__ void store1(int k, const Slot& v) { a[k] = v; }
+  static __device__ __forceinline__ void update1(Slot& s, float A, float gx, float gy, float gz) {
+    s.x += A; s.y += gx; s.z += gy; s.w += gz;
   }
-  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
-    a[k1] = s.v1;
-    a[k2] = s.v2;
-    a[k3] = s.v3;
+  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
+    return make_float4(c ? x.x : y.x, c ? x.y : y.y, c ? x.z : y.z, c ? x.w : y.w);
   }
   // sums over the row's slots t, t + R, ... (len of them) except slot kd
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>* r) const {
@@ -429,25 +423,22 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     acc1(h.z, l.z, gy);
     acc1(h.w, l.w, gz);
   }
-  struct Slots {
-    float4 h1, h2, h3, l1, l2, l3;
+  struct Slot {
+    float4 h, l;  // leading parts and error terms of A and the three sums of c_i
   };
-  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const {
-    return {hi[k1], hi[k2], hi[k3], lo[k1], lo[k2], lo[k3]};
+  __device__ __forceinline__ Slot load1(int k) const { return {hi[k], lo[k]}; }
+  __device__ __forceinline__ void store1(int k, const Slot& v) {
+    hi[k] = v.h;
+    lo[k] = v.l;
   }
-  static __device__ __forceinline__ void update(Slots& s, float A1, float A2, float A3, float gx, float gy,
-                                                float gz) {
-    acc4(s.h1, s.l1, A1, gx, gy, gz);
-    acc4(s.h2, s.l2, A2, gx, gy, gz);
-    acc4(s.h3, s.l3, A3, gx, gy, gz);
+  static __device__ __forceinline__ void update1(Slot& s, float A, float gx, float gy, float gz) {
+    acc4(s.h, s.l, A, gx, gy, gz);
   }
-  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
-    hi[k1] = s.h1;
-    hi[k2] = s.h2;
-    hi[k3] = s.h3;
-    lo[k1] = s.l1;
-    lo[k2] = s.l2;
-    lo[k3] = s.l3;
+  static __device__ __forceinline__ float4 pick4(bool c, const float4& x, const float4& y) {
+    return make_float4(c ? x.x : y.x, c ? x.y : y.y, c ? x.z : y.z, c ? x.w : y.w);
+  }
+  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
+    return {pick4(c, x.h, y.h), pick4(c, x.l, y.l)};
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -513,21 +504,19 @@ struct AccSmem<NSI_FP64> {
     a0[k] = {0.0, 0.0};
     a1[k] = {0.0, 0.0};
   }
-  struct Slots {
-    T2<double> x1, x2, x3, y1, y2, y3;
+  struct Slot {
+    T2<double> x, y;  // (A, sum c_i x), (sum c_i y, sum c_i z)
   };
-  __device__ __forceinline__ Slots load3(int k1, int k2, int k3) const {
-    return {a0[k1], a0[k2], a0[k3], a1[k1], a1[k2], a1[k3]};
+  __device__ __forceinline__ Slot load1(int k) const { return {a0[k], a1[k]}; }
+  __device__ __forceinline__ void store1(int k, const Slot& v) {
+    a0[k] = v.x;
+    a1[k] = v.y;
   }
-  static __device__ __forceinline__ void update(Slots& s, double A1, double A2, double A3, double gx, double gy,
-                                                double gz) {
-    s.x1.x += A1; s.x1.y += gx; s.y1.x += gy; s.y1.y += gz;
-    s.x2.x += A2; s.x2.y += gx; s.y2.x += gy; s.y2.y += gz;
-    s.x3.x += A3; s.x3.y += gx; s.y3.x += gy; s.y3.y += gz;
+  static __device__ __forceinline__ void update1(Slot& s, double A, double gx, double gy, double gz) {
+    s.x.x += A; s.x.y += gx; s.y.x += gy; s.y.y += gz;
   }
-  __device__ __forceinline__ void store3(int k1, int k2, int k3, const Slots& s) {
-    a0[k1] = s.x1; a0[k2] = s.x2; a0[k3] = s.x3;
-    a1[k1] = s.y1; a1[k2] = s.y2; a1[k3] = s.y3;
+  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
+    return {{c ? x.x.x : y.x.x, c ? x.x.y : y.x.y}, {c ? x.y.x : y.y.x, c ? x.y.y : y.y.y}};
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_FP64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -562,81 +551,104 @@ __device__ __forceinline__ void* staged_half(unsigned char* smem, const GatherSm
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 
-// Contribution of one element of row i's star, with node i as the origin.
-// With w = rho/120 (S + u_i) + mu/(6 det) c_i, the convection + viscous part
-// of A_e[i][j] is w . c_j (nsi_internal.cuh); the pressure-gradient part of
-// every entry of the row is -c_i / 24 (scaled at write-out); the element's
-// lumped mass is rho det / (24 dt) (det summed, scaled at the end).
-template <typename T>
-struct StarContrib {
-  int k1, k2, k3;  // slots of the three other nodes
-  T A1, A2, A3;
-  V3<T> ci;
-  T det;
+// The element walk of one row (the element loop of phase 2), node i as the
+// origin.  A window of two neighbours (p, q) stays in registers with their
+// edge vectors, velocities and accumulators; every step brings one node c in
+// from shared memory, evaluates the element (i, p, q, c) if the step says so,
+// writes back the accumulator of the node that leaves the window and keeps
+// the other two.  With c_p = d_q x d_c, c_q = d_c x d_p, c_c = d_p x d_q
+// (cofactors of the Jacobian, calculate_cartesian_derivatives, for the order
+// (p, q, c)), det = d_p . c_p and c_i = -(c_p + c_q + c_c), the element adds
+//   A(i,x) += w . c_x  (x = p, q, c),  w = rho/120 (2 u_i + u_p + u_q + u_c) + mu/(6 det) c_i
+// and c_i to the three pressure-gradient sums and det to the lumped mass sum
+// (scaled at write-out).  For the order (p, q, c) an odd permutation of the
+// element's own, det and every cofactor change sign, w does not, so every
+// contribution is multiplied by -1.  c_c is the cofactor that the previous
+// step computed for the node that left: it is carried, not recomputed.
+template <typename T, typename Slot>
+struct WalkNode {
+  int k;  // shared-memory slot
+  V3<T> d, u;
+  Slot v;
 };
 
-template <typename T>
-__device__ __forceinline__ StarContrib<T> star_contrib(unsigned w, const T4<T>* __restrict__ nb0,
-                                                       const T2<T>* __restrict__ nb1, int t, int R,
-                                                       const V3<T>& u2i, T kc, T kmu) {
-  StarContrib<T> r;
-  r.k1 = (int)(w & 31) * R + t;
-  r.k2 = (int)((w >> 5) & 31) * R + t;
-  r.k3 = (int)((w >> 10) & 31) * R + t;
-  const T4<T> a1 = nb0[r.k1], a2 = nb0[r.k2], a3 = nb0[r.k3];
-  const T2<T> b1 = nb1[r.k1], b2 = nb1[r.k2], b3 = nb1[r.k3];
-  const V3<T> d1{a1.x, a1.y, a1.z}, d2{a2.x, a2.y, a2.z}, d3{a3.x, a3.y, a3.z};
-  // Jacobian cofactors (calculate_cartesian_derivatives) with i as the origin
-  const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
-  r.det = dot(d1, c1);
-  r.ci = {-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
-  const T kv = kmu * rcp_fast(r.det);
-  // w = rho/120 (2 u_i + u_1 + u_2 + u_3) + mu/(6 det) c_i
-  const V3<T> w3{kc * (u2i.x + a1.w + a2.w + a3.w) + kv * r.ci.x, kc * (u2i.y + b1.x + b2.x + b3.x) + kv * r.ci.y,
-                 kc * (u2i.z + b1.y + b2.y + b3.y) + kv * r.ci.z};
-  r.A1 = dot(w3, c1);
-  r.A2 = dot(w3, c2);
-  r.A3 = dot(w3, c3);
-  return r;
-}
-
-template <int P, bool DEBUG>
-__device__ __forceinline__ bool star_ok(unsigned w, int len) {
-  return !DEBUG || ((int)(w & 31) < len && (int)((w >> 5) & 31) < len && (int)((w >> 10) & 31) < len);
-}
-
-// the element loop of one row, software-pipelined one element deep: the
-// accumulator loads of element s are in flight while element s + 1 is
-// computed (it reads only the neighbour records), then element s is stored
-template <int P, bool DEBUG>
-__device__ __forceinline__ void star_loop(const uint16_t* __restrict__ star, int s0, int s1, int len,
-                                          const T4<typename Prec<P>::T>* __restrict__ nb0,
-                                          const T2<typename Prec<P>::T>* __restrict__ nb1, AccSmem<P>& acc, int t,
-                                          int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
-                                          typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
+template <int P>
+__device__ __forceinline__ WalkNode<typename Prec<P>::T, typename AccSmem<P>::Slot> walk_load(
+    int k, const T4<typename Prec<P>::T>* __restrict__ nb0, const T2<typename Prec<P>::T>* __restrict__ nb1,
+    const AccSmem<P>& acc) {
   using T = typename Prec<P>::T;
+  const T4<T> a = nb0[k];
+  const T2<T> b = nb1[k];
+  return {k, {a.x, a.y, a.z}, {a.w, b.x, b.y}, acc.load1(k)};
+}
+
+template <int P, bool DEBUG>
+__device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nsteps, int len, int kd,
+                                         const T4<typename Prec<P>::T>* __restrict__ nb0,
+                                         const T2<typename Prec<P>::T>* __restrict__ nb1, AccSmem<P>& acc, int t,
+                                         int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
+                                         typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
+  using T = typename Prec<P>::T;
+  using Slot = typename AccSmem<P>::Slot;
+  using Node = WalkNode<T, Slot>;
+  if (nsteps <= 0) return;
   if (DEBUG) {
     bool ok = true;
-    for (int s = s0; s < s1; ++s) ok &= star_ok<P, DEBUG>(star[s], len);
+    for (int s = 0; s < nsteps; ++s) ok &= (int)(st[s] & WALK_POS) < len;
     if (!ok) {
       atomicOr(err, ERR_STAR);
       return;
     }
   }
-  if (s0 >= s1) return;
-  StarContrib<T> a = star_contrib<T>(star[s0], nb0, nb1, t, R, u2i, kc, kmu);
-  for (int s = s0 + 1; s < s1; ++s) {
-    typename AccSmem<P>::Slots v = acc.load3(a.k1, a.k2, a.k3);
-    const StarContrib<T> b = star_contrib<T>(star[s], nb0, nb1, t, R, u2i, kc, kmu);
-    AccSmem<P>::update(v, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
-    acc.store3(a.k1, a.k2, a.k3, v);
-    detsum.add(a.det);
-    a = b;
+  // the window starts on the diagonal slot (edge vector 0, accumulator 0)
+  Node p = walk_load<P>(kd, nb0, nb1, acc);
+  Node q = p;
+  V3<T> cpq{T(0), T(0), T(0)};  // d_p x d_q
+  unsigned w = st[0];
+  Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
+  for (int s = 0; s < nsteps; ++s) {
+    // the next step's node, in flight while this element is evaluated (it is
+    // never one of p, q, c: the walk is encoded that way)
+    unsigned wn = w;
+    Node cn = c;
+    if (s + 1 < nsteps) {
+      wn = st[s + 1];
+      cn = walk_load<P>((int)(wn & WALK_POS) * R + t, nb0, nb1, acc);
+    }
+    const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);
+    const bool elem = (w & WALK_ELEM) != 0u;
+    const T det = dot(p.d, cp);
+    const V3<T> ci{-(cp.x + cq.x + cpq.x), -(cp.y + cq.y + cpq.y), -(cp.z + cq.z + cpq.z)};
+    const T kv = kmu * rcp_fast(elem ? det : T(1));
+    const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x, kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
+                   kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
+    // +-1 for the orientation, 0 for a step that only moves the window
+    const T f = elem ? ((w & WALK_NEG) ? T(-1) : T(1)) : T(0);
+    const T gx = f * ci.x, gy = f * ci.y, gz = f * ci.z;
+    AccSmem<P>::update1(p.v, f * dot(w3, cp), gx, gy, gz);
+    AccSmem<P>::update1(q.v, f * dot(w3, cq), gx, gy, gz);
+    AccSmem<P>::update1(c.v, f * dot(w3, cpq), gx, gy, gz);
+    detsum.add(f * det);
+    // q leaves (window (c, p), carried cofactor d_c x d_p = c_q) or p leaves
+    // (window (q, c), carried d_q x d_c = c_p)
+    const bool evq = (w & WALK_EVQ) != 0u;
+    acc.store1(evq ? q.k : p.k, AccSmem<P>::pick(evq, q.v, p.v));
+    const Node np{evq ? c.k : q.k,
+                  {evq ? c.d.x : q.d.x, evq ? c.d.y : q.d.y, evq ? c.d.z : q.d.z},
+                  {evq ? c.u.x : q.u.x, evq ? c.u.y : q.u.y, evq ? c.u.z : q.u.z},
+                  AccSmem<P>::pick(evq, c.v, q.v)};
+    const Node nq{evq ? p.k : c.k,
+                  {evq ? p.d.x : c.d.x, evq ? p.d.y : c.d.y, evq ? p.d.z : c.d.z},
+                  {evq ? p.u.x : c.u.x, evq ? p.u.y : c.u.y, evq ? p.u.z : c.u.z},
+                  AccSmem<P>::pick(evq, p.v, c.v)};
+    cpq = V3<T>{evq ? cq.x : cp.x, evq ? cq.y : cp.y, evq ? cq.z : cp.z};
+    p = np;
+    q = nq;
+    c = cn;
+    w = wn;
   }
-  typename AccSmem<P>::Slots v = acc.load3(a.k1, a.k2, a.k3);
-  AccSmem<P>::update(v, a.A1, a.A2, a.A3, a.ci.x, a.ci.y, a.ci.z);
-  acc.store3(a.k1, a.k2, a.k3, v);
-  detsum.add(a.det);
+  acc.store1(p.k, p.v);
+  acc.store1(q.k, q.v);
 }
 
 // one block of rows [r0, r0 + blockDim.x) of one mesh
@@ -651,7 +663,7 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   const int nrows = (int)(r_end - r0);
   const int32_t base = m.row_ptr[r0], bend = m.row_ptr[r_end];
   const int L = bend - base;
-  const int32_t sbase = m.star_ptr[r0], send = m.star_ptr[r_end];
+  const int32_t sbase = m.walk_ptr[r0], send = m.walk_ptr[r_end];
   const int S = send - sbase;
   if (DEBUG && (L > lay.L || S > lay.S || R != lay.R)) {
     if (t == 0) atomicOr(m.err, ERR_STAR);
@@ -661,32 +673,32 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   T2<T>* __restrict__ nb1 = reinterpret_cast<T2<T>*>(smem + lay.nb1());
   AccSmem<P> acc(smem + lay.acc(), lay.N());
   int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
-  uint16_t* star = reinterpret_cast<uint16_t*>(smem + lay.star());
+  uint8_t* walk = smem + lay.walk();
   const T kc = kc_of<T>(f);
   const T kmu = kmu_of<T>(f);
   const T kmass = kmass_of<T>(f);
   const T kg = (T)(-1.0 / 24.0);
 
-  // phase 0: the row's scalars and the entry -> row map; the block's column
-  // indices and row-gather words by asynchronous copies (all in flight)
+  // phase 0: the row's scalars; the block's column indices and walk steps by
+  // asynchronous copies (all in flight)
   const int64_t i = r0 + t;
   int32_t rs = 0, re = 0, s0 = 0, s1 = 0;
   int dp = 0;
   V3<T> uni{T(0), T(0), T(0)};
-  const int soff = sbase & 1;  // star words are copied as aligned pairs
+  const int soff = sbase & 3;  // walk bytes are copied as aligned 4-byte words
   if (t < nrows) {
     rs = m.row_ptr[i];
     re = m.row_ptr[i + 1];
-    s0 = m.star_ptr[i] - sbase + soff;
-    s1 = m.star_ptr[i + 1] - sbase + soff;
+    s0 = m.walk_ptr[i] - sbase + soff;
+    s1 = m.walk_ptr[i + 1] - sbase + soff;
     dp = m.diag_pos[i];
     uni = load_vec<T>(f.un, i);
   }
   for (int k = t; k < L; k += R) cp_async4(&col[k], m.col_idx + base + k);
   {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(m.star + (sbase - soff));
-    const int words = (S + soff + 1) >> 1;
-    for (int k = t; k < words; k += R) cp_async4(reinterpret_cast<uint32_t*>(star) + k, src + k);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(m.walk + (sbase - soff));
+    const int words = (S + soff + 3) >> 2;
+    for (int k = t; k < words; k += R) cp_async4(reinterpret_cast<uint32_t*>(walk) + k, src + k);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -755,7 +767,7 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
       const T4<T> di = nb0[kd];
       const T2<T> ei = nb1[kd];
       const V3<T> u2i{di.w + di.w, ei.x + ei.x, ei.y + ei.y};
-      star_loop<P, DEBUG>(star, s0, s1, len, nb0, nb1, acc, t, R, u2i, kc, kmu, detsum, m.err);
+      walk_row<P, DEBUG>(walk + s0, s1 - s0, len, kd, nb0, nb1, acc, t, R, u2i, kc, kmu, detsum, m.err);
       // diagonal from the partition of unity (sum_b grad N_b = 0, exact):
       //   A(i,i) = lumped mass - sum_{j != i} A(i,j)   (convection + viscous parts)
       //   G(i,i) = 1/3 sum_{j != i} G(i,j)            (each element adds c_i to three
@@ -1388,7 +1400,7 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
     return check_launch("fan_kernel");
   }
   const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
   const size_t smem = lay.total();
   if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
   if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
@@ -1461,16 +1473,33 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
     batched_fan_kernel<P><<<grid, FAN_BLOCK, fsm, s>>>(args);
     return check_launch("batched_fan_kernel");
   }
-  // one block size for the whole batch: the smallest planned one.  A mesh's
-  // per-block maxima, taken over blocks of its own (larger or equal) size,
-  // bound its blocks of the smaller size too.
-  int R = 1 << 30, max_entries = 0, max_stars = 0, max_row = 1;
-  for (int k = 0; k < count; ++k) R = std::min(R, hs[k]->plan.rows_per_block);
+  // one block size for the whole batch: the largest one, no larger than any
+  // mesh's own choice, that every mesh has planned (the per-block maxima of
+  // the shared-memory layout are those of that size: blocks of different
+  // sizes do not nest)
+  int Rmin = 1 << 30, R = 0, max_entries = 0, max_steps = 0, max_row = 1;
+  for (int k = 0; k < count; ++k) Rmin = std::min(Rmin, hs[k]->plan.rows_per_block);
+  const GatherPlan* use[NSI_MAX_BATCH] = {};
+  for (int cand : {128, 96, 64, 32}) {
+    if (cand > Rmin) continue;
+    bool all = true;
+    for (int k = 0; k < count && all; ++k) {
+      use[k] = nullptr;
+      for (int j = 0; j < hs[k]->n_plans; ++j)
+        if (hs[k]->plans[j].rows_per_block == cand) use[k] = &hs[k]->plans[j];
+      all = use[k] != nullptr;
+    }
+    if (all) {
+      R = cand;
+      break;
+    }
+  }
+  if (R == 0) return fail(NSI_ERR_UNSUPPORTED, "no block size is planned for every mesh of the batch");
   int64_t blocks = 0;
   for (int k = 0; k < count; ++k) {
     const NsiHandle* h = hs[k];
-    max_entries = std::max(max_entries, h->plan.max_block_entries);
-    max_stars = std::max(max_stars, h->plan.max_block_stars);
+    max_entries = std::max(max_entries, use[k]->max_block_entries);
+    max_steps = std::max(max_steps, use[k]->max_block_steps);
     max_row = std::max(max_row, h->max_row);
     args.item[k].m = view_of(h);
     args.item[k].f = fields_of(&fs[k]);
@@ -1484,7 +1513,7 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
     pack_kernel<P><<<(hs[k]->n + 255) / 256, 256, 0, s>>>(args.item[k].m, args.item[k].f, hs[k]->rec);
   nsi_status st = set_gather_smem<P, false>();
   if (st) return st;
-  const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_stars);
+  const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_steps);
   const size_t smem = lay.total();
   if (smem > 200 * 1024) return fail(NSI_ERR_UNSUPPORTED, "batched meshes need more shared memory than a block has");
   int per_sm = 0, sms = 0, dev = 0;
@@ -1566,7 +1595,7 @@ static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const Out
     return check_launch("fan_kernel (no-alloc)");
   }
   const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_stars);
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
   gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay);
   return check_launch("gather_kernel (no-alloc)");
 }
