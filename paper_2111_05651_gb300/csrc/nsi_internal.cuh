@@ -42,7 +42,7 @@ constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
 constexpr unsigned WALK_POS = 31u;       // bits 0-4: row position of the new node
 constexpr unsigned WALK_ELEM = 1u << 5;  // the step evaluates element (p, q, c)
 constexpr unsigned WALK_NEG = 1u << 6;   // (p, q, c) is an odd permutation of the element's order
-constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves (window becomes (c, p)); else p leaves (window (q, c))
+constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves, c takes its place (window (p, c)); else p leaves (window (c, q))
 
 // Edge-fan map: for every off-diagonal CSR entry (i, j), the ring of nodes
 // around the edge (i, j) -- the other two nodes of every element containing

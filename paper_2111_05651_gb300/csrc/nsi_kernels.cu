@@ -345,12 +345,14 @@ struct Acc<NSI_MIXED_F32_ACC64> {
 
 __device__ __forceinline__ void store_acc(double* p, const Acc<NSI_FP64>& a) { *p = a.v; }
 __device__ __forceinline__ void store_acc(float* p, const Acc<NSI_MIXED_F32_ACC32>& a) { *p = a.v; }
-__device__ __forceinline__ void store_acc(double* p, const Acc<NSI_MIXED_F32_ACC64>& a) {
-  // renormalise the pair (Fast2Sum) so that |lo| <= ulp(hi)/2, then build the double
-  const float s = a.hi + a.lo;
-  const float lo = a.lo - (s - a.hi);
-  *reinterpret_cast<long long*>(p) = pair_to_f64_bits(s, lo);
+// the double nearest hi + lo: the pair is renormalised first (Fast2Sum, so
+// that |lo| <= ulp(hi)/2), then the double is built from its bits
+__device__ __forceinline__ double pair_double(float hi, float lo) {
+  const float s = hi + lo;
+  const float l = lo - (s - hi);
+  return __longlong_as_double(pair_to_f64_bits(s, l));
 }
+__device__ __forceinline__ void store_acc(double* p, const Acc<NSI_MIXED_F32_ACC64>& a) { *p = pair_double(a.hi, a.lo); }
 
 template <typename T>
 struct alignas(4 * sizeof(T)) T4 {
@@ -369,36 +371,57 @@ struct alignas(2 * sizeof(T)) T2 {
 // three loads are issued before the stores.
 template <int P>
 struct AccSmem;
+// paired float arithmetic (one instruction for two lanes of a float2, each
+// rounded like its scalar counterpart); a - b is formed as b * (-1) + a with a
+// single rounding
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// error-free sum of pairs (TwoSum lane by lane): h + x = s + e exactly; s
+// replaces h and e is added to the error term l
+__device__ __forceinline__ void two_sum2(float2& h, float2& l, float2 x) {
+  const float2 s = add2(h, x);
+  const float2 bb = sub2(s, h);
+  const float2 e = add2(sub2(h, sub2(s, bb)), sub2(x, bb));
+  h = s;
+  l = add2(l, e);
+}
+
+// Float slots hold (sum c_i x, sum c_i y, sum c_i z, A): the two halves are
+// the pairs (G_x, G_y) and (G_z, A) of the paired updates.
 template <>
 struct AccSmem<NSI_MIXED_F32_ACC32> {
   float4* __restrict__ a;
   __device__ __forceinline__ AccSmem(unsigned char* p, size_t) : a(reinterpret_cast<float4*>(p)) {}
   __device__ __forceinline__ void zero(int k) { a[k] = make_float4(0.f, 0.f, 0.f, 0.f); }
-  using Slot = float4;  // A, sum c_i x, sum c_i y, sum c_i z
-  __device__ __forceinline__ Slot load1(int k) const { return a[k]; }
-  __device__ __forceinline__ void store1(int k, const Slot& v) { a[k] = v; }
-  static __device__ __forceinline__ void update1(Slot& s, float A, float gx, float gy, float gz) {
-    s.x += A; s.y += gx; s.z += gy; s.w += gz;
+  struct Slot {
+    float2 g, r;  // (G_x, G_y), (G_z, A)
+  };
+  __device__ __forceinline__ Slot load1(int k) const {
+    const float4 v = a[k];
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
   }
-  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
-    return make_float4(c ? x.x : y.x, c ? x.y : y.y, c ? x.z : y.z, c ? x.w : y.w);
+  __device__ __forceinline__ void store1(int k, const Slot& v) { a[k] = make_float4(v.g.x, v.g.y, v.r.x, v.r.y); }
+  static __device__ __forceinline__ void add(Slot& s, float2 gxy, float2 gz_a) {
+    s.g = add2(s.g, gxy);
+    s.r = add2(s.r, gz_a);
   }
   // sums over the row's slots t, t + R, ... (len of them) except slot kd
+  // (r[0]: A, r[1..3]: G_x..G_z)
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
       if (k == kd) continue;
       const float4 v = a[k];
-      r[0].add(v.x); r[1].add(v.y); r[2].add(v.z); r[3].add(v.w);
+      r[0].add(v.w); r[1].add(v.x); r[2].add(v.y); r[3].add(v.z);
     }
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>* r) {
-    a[k] = make_float4(r[0].v, r[1].v, r[2].v, r[3].v);
+    a[k] = make_float4(r[1].v, r[2].v, r[3].v, r[0].v);
   }
   // finished value of component C (0: A, 1..3: G_x..G_z) of slot k
   template <int C>
   __device__ __forceinline__ float value(int k, float kg) const {
     const float4 v = a[k];
-    return C == 0 ? v.x : kg * (C == 1 ? v.y : C == 2 ? v.z : v.w);
+    return C == 0 ? v.w : kg * (C == 1 ? v.x : C == 2 ? v.y : v.z);
   }
 };
 template <>
@@ -411,87 +434,44 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     hi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  static __device__ __forceinline__ void acc1(float& h, float& l, float x) {
-    float s, e;
-    two_sum(h, x, s, e);
-    h = s;
-    l += e;
-  }
-  static __device__ __forceinline__ void acc4(float4& h, float4& l, float A, float gx, float gy, float gz) {
-    acc1(h.x, l.x, A);
-    acc1(h.y, l.y, gx);
-    acc1(h.z, l.z, gy);
-    acc1(h.w, l.w, gz);
-  }
   struct Slot {
-    float4 h, l;  // leading parts and error terms of A and the three sums of c_i
+    float2 hg, hr, lg, lr;  // leading parts and error terms of (G_x, G_y) and (G_z, A)
   };
-  __device__ __forceinline__ Slot load1(int k) const { return {hi[k], lo[k]}; }
+  __device__ __forceinline__ Slot load1(int k) const {
+    const float4 h = hi[k], l = lo[k];
+    return {make_float2(h.x, h.y), make_float2(h.z, h.w), make_float2(l.x, l.y), make_float2(l.z, l.w)};
+  }
   __device__ __forceinline__ void store1(int k, const Slot& v) {
-    hi[k] = v.h;
-    lo[k] = v.l;
+    hi[k] = make_float4(v.hg.x, v.hg.y, v.hr.x, v.hr.y);
+    lo[k] = make_float4(v.lg.x, v.lg.y, v.lr.x, v.lr.y);
   }
-  static __device__ __forceinline__ void update1(Slot& s, float A, float gx, float gy, float gz) {
-    acc4(s.h, s.l, A, gx, gy, gz);
-  }
-  static __device__ __forceinline__ float4 pick4(bool c, const float4& x, const float4& y) {
-    return make_float4(c ? x.x : y.x, c ? x.y : y.y, c ? x.z : y.z, c ? x.w : y.w);
-  }
-  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
-    return {pick4(c, x.h, y.h), pick4(c, x.l, y.l)};
+  static __device__ __forceinline__ void add(Slot& s, float2 gxy, float2 gz_a) {
+    two_sum2(s.hg, s.lg, gxy);
+    two_sum2(s.hr, s.lr, gz_a);
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
       if (k == kd) continue;
       const float4 h = hi[k], l = lo[k];
-      r[0].add(h.x); r[1].add(h.y); r[2].add(h.z); r[3].add(h.w);
-      r[0].lo += l.x; r[1].lo += l.y; r[2].lo += l.z; r[3].lo += l.w;
+      r[0].add(h.w); r[1].add(h.x); r[2].add(h.y); r[3].add(h.z);
+      r[0].lo += l.w; r[1].lo += l.x; r[2].lo += l.y; r[3].lo += l.z;
     }
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>* r) {
-    hi[k] = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
-    lo[k] = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
+    hi[k] = make_float4(r[1].hi, r[2].hi, r[3].hi, r[0].hi);
+    lo[k] = make_float4(r[1].lo, r[2].lo, r[3].lo, r[0].lo);
   }
-  // convert slot k in place: the slot's 32 bytes become the four finished
-  // doubles (A, G_x in the hi half; G_y, G_z in the lo half)
-  __device__ __forceinline__ void finalize_inplace(int k, float kg) {
-    const float4 h4 = hi[k], l4 = lo[k];
-    Acc<NSI_MIXED_F32_ACC64> t;
-    double r[4];
-    t.hi = h4.x;
-    t.lo = l4.x;
-    store_acc(&r[0], t);
-    const float hv[3] = {h4.y, h4.z, h4.w}, lv[3] = {l4.y, l4.z, l4.w};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {  // kg * (hi + lo), keeping the product error of the leading part
-      const float p = kg * hv[c];
-      t.hi = p;
-      t.lo = fmaf(kg, hv[c], -p) + kg * lv[c];
-      store_acc(&r[c + 1], t);
-    }
-    reinterpret_cast<double2*>(hi)[k] = make_double2(r[0], r[1]);
-    reinterpret_cast<double2*>(lo)[k] = make_double2(r[2], r[3]);
-  }
-  __device__ __forceinline__ double2 finished(int k, int half) const {
-    return reinterpret_cast<const double2*>(half ? lo : hi)[k];
-  }
-  template <int C>
-  __device__ __forceinline__ double value(int k, float kg) const {
-    const float4 h4 = hi[k], l4 = lo[k];
-    const float h = C == 0 ? h4.x : C == 1 ? h4.y : C == 2 ? h4.z : h4.w;
-    const float l = C == 0 ? l4.x : C == 1 ? l4.y : C == 2 ? l4.z : l4.w;
-    Acc<NSI_MIXED_F32_ACC64> t;
-    if (C == 0) {
-      t.hi = h;
-      t.lo = l;
-    } else {  // kg * (hi + lo), keeping the product error of the leading part
-      const float p = kg * h;
-      t.hi = p;
-      t.lo = fmaf(kg, h, -p) + kg * l;
-    }
-    double d;
-    store_acc(&d, t);
-    return d;
+  // (leading, error) pairs of one half of slot k: half 0 gives G_x and G_y,
+  // half 1 gives G_z and A.  The pressure-gradient sums are scaled by kg with
+  // the product error of the leading part kept.
+  __device__ __forceinline__ float4 pairs(int k, int half, float kg) const {
+    const float2 h = reinterpret_cast<const float2*>(hi)[2 * k + half];
+    const float2 l = reinterpret_cast<const float2*>(lo)[2 * k + half];
+    const float p0 = kg * h.x;
+    const float2 g0 = make_float2(p0, fmaf(kg, h.x, -p0) + kg * l.x);
+    if (half == 1) return make_float4(g0.x, g0.y, h.y, l.y);
+    const float p1 = kg * h.y;
+    return make_float4(g0.x, g0.y, p1, fmaf(kg, h.y, -p1) + kg * l.y);
   }
 };
 template <>
@@ -514,9 +494,6 @@ struct AccSmem<NSI_FP64> {
   }
   static __device__ __forceinline__ void update1(Slot& s, double A, double gx, double gy, double gz) {
     s.x.x += A; s.x.y += gx; s.y.x += gy; s.y.y += gz;
-  }
-  static __device__ __forceinline__ Slot pick(bool c, const Slot& x, const Slot& y) {
-    return {{c ? x.x.x : y.x.x, c ? x.x.y : y.x.y}, {c ? x.y.x : y.y.x, c ? x.y.y : y.y.y}};
   }
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_FP64>* r) const {
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -555,16 +532,18 @@ __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 // origin.  A window of two neighbours (p, q) stays in registers with their
 // edge vectors, velocities and accumulators; every step brings one node c in
 // from shared memory, evaluates the element (i, p, q, c) if the step says so,
-// writes back the accumulator of the node that leaves the window and keeps
-// the other two.  With c_p = d_q x d_c, c_q = d_c x d_p, c_c = d_p x d_q
-// (cofactors of the Jacobian, calculate_cartesian_derivatives, for the order
-// (p, q, c)), det = d_p . c_p and c_i = -(c_p + c_q + c_c), the element adds
+// then writes back the accumulator of the node that leaves the window and
+// puts c in its registers (the window stays (p, q) in register order).  With
+// c_p = d_q x d_c, c_q = d_c x d_p, c_c = d_p x d_q (cofactors of the
+// Jacobian, calculate_cartesian_derivatives, for the order (p, q, c)),
+// det = d_p . c_p and c_i = -(c_p + c_q + c_c), the element adds
 //   A(i,x) += w . c_x  (x = p, q, c),  w = rho/120 (2 u_i + u_p + u_q + u_c) + mu/(6 det) c_i
 // and c_i to the three pressure-gradient sums and det to the lumped mass sum
 // (scaled at write-out).  For the order (p, q, c) an odd permutation of the
 // element's own, det and every cofactor change sign, w does not, so every
-// contribution is multiplied by -1.  c_c is the cofactor that the previous
-// step computed for the node that left: it is carried, not recomputed.
+// contribution is multiplied by -1.  c_c is carried from the previous step:
+// after p leaves, the window (c, q) has d_c x d_q = -c_p; after q leaves,
+// (p, c) has d_p x d_c = -c_q; m holds c_p or c_q, and c_c = -m.
 template <typename T, typename Slot>
 struct WalkNode {
   int k;  // shared-memory slot
@@ -589,8 +568,7 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
                                          int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
                                          typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
   using T = typename Prec<P>::T;
-  using Slot = typename AccSmem<P>::Slot;
-  using Node = WalkNode<T, Slot>;
+  using Node = WalkNode<T, typename AccSmem<P>::Slot>;
   if (nsteps <= 0) return;
   if (DEBUG) {
     bool ok = true;
@@ -603,47 +581,57 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   // the window starts on the diagonal slot (edge vector 0, accumulator 0)
   Node p = walk_load<P>(kd, nb0, nb1, acc);
   Node q = p;
-  V3<T> cpq{T(0), T(0), T(0)};  // d_p x d_q
+  V3<T> m{T(0), T(0), T(0)};
   unsigned w = st[0];
   Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
   for (int s = 0; s < nsteps; ++s) {
-    // the next step's node, in flight while this element is evaluated (it is
-    // never one of p, q, c: the walk is encoded that way)
-    unsigned wn = w;
-    Node cn = c;
-    if (s + 1 < nsteps) {
-      wn = st[s + 1];
-      cn = walk_load<P>((int)(wn & WALK_POS) * R + t, nb0, nb1, acc);
-    }
+    // the next step's node, in flight while this element is evaluated (never
+    // one of p, q, c: the walk is encoded that way; the last step reloads its
+    // own node, unused)
+    const unsigned wn = st[s + 1 < nsteps ? s + 1 : s];
+    const Node cn = walk_load<P>((int)(wn & WALK_POS) * R + t, nb0, nb1, acc);
     const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);
     const bool elem = (w & WALK_ELEM) != 0u;
-    const T det = dot(p.d, cp);
-    const V3<T> ci{-(cp.x + cq.x + cpq.x), -(cp.y + cq.y + cpq.y), -(cp.z + cq.z + cpq.z)};
-    const T kv = kmu * rcp_fast(elem ? det : T(1));
-    const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x, kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
-                   kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
-    // +-1 for the orientation, 0 for a step that only moves the window
-    const T f = elem ? ((w & WALK_NEG) ? T(-1) : T(1)) : T(0);
-    const T gx = f * ci.x, gy = f * ci.y, gz = f * ci.z;
-    AccSmem<P>::update1(p.v, f * dot(w3, cp), gx, gy, gz);
-    AccSmem<P>::update1(q.v, f * dot(w3, cq), gx, gy, gz);
-    AccSmem<P>::update1(c.v, f * dot(w3, cpq), gx, gy, gz);
-    detsum.add(f * det);
-    // q leaves (window (c, p), carried cofactor d_c x d_p = c_q) or p leaves
-    // (window (q, c), carried d_q x d_c = c_p)
-    const bool evq = (w & WALK_EVQ) != 0u;
-    acc.store1(evq ? q.k : p.k, AccSmem<P>::pick(evq, q.v, p.v));
-    const Node np{evq ? c.k : q.k,
-                  {evq ? c.d.x : q.d.x, evq ? c.d.y : q.d.y, evq ? c.d.z : q.d.z},
-                  {evq ? c.u.x : q.u.x, evq ? c.u.y : q.u.y, evq ? c.u.z : q.u.z},
-                  AccSmem<P>::pick(evq, c.v, q.v)};
-    const Node nq{evq ? p.k : c.k,
-                  {evq ? p.d.x : c.d.x, evq ? p.d.y : c.d.y, evq ? p.d.z : c.d.z},
-                  {evq ? p.u.x : c.u.x, evq ? p.u.y : c.u.y, evq ? p.u.z : c.u.z},
-                  AccSmem<P>::pick(evq, p.v, c.v)};
-    cpq = V3<T>{evq ? cq.x : cp.x, evq ? cq.y : cp.y, evq ? cq.z : cp.z};
-    p = np;
-    q = nq;
+    if constexpr (P == NSI_FP64) {
+      if (elem) {  // (steps that only fill the window come first in a row: warp-uniform)
+        const T det = dot(p.d, cp);
+        const V3<T> ci{m.x - cp.x - cq.x, m.y - cp.y - cq.y, m.z - cp.z - cq.z};
+        const T kv = kmu * rcp_fast(det);
+        const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
+                       kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
+                       kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
+        const T f = (w & WALK_NEG) ? T(-1) : T(1);  // orientation
+        const T gx = f * ci.x, gy = f * ci.y, gz = f * ci.z;
+        AccSmem<P>::update1(p.v, f * dot(w3, cp), gx, gy, gz);
+        AccSmem<P>::update1(q.v, f * dot(w3, cq), gx, gy, gz);
+        AccSmem<P>::update1(c.v, -f * dot(w3, m), gx, gy, gz);
+        detsum.add(f * det);
+      }
+    } else {
+      // branch-free: a step that only fills the window adds zeros
+      const float det = dot(p.d, cp);
+      const V3<float> ci{m.x - cp.x - cq.x, m.y - cp.y - cq.y, m.z - cp.z - cq.z};
+      const float kv = kmu * rcp_fast(elem ? det : 1.0f);
+      const V3<float> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
+                         kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
+                         kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
+      const float f = elem ? ((w & WALK_NEG) ? -1.0f : 1.0f) : 0.0f;  // orientation, or 0
+      const float2 ff = make_float2(f, f);
+      const float2 gxy = __fmul2_rn(make_float2(ci.x, ci.y), ff);
+      AccSmem<P>::add(p.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cp)), ff));
+      AccSmem<P>::add(q.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cq)), ff));
+      AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(f, -f)));
+      detsum.add(f * det);
+    }
+    if (w & WALK_EVQ) {
+      acc.store1(q.k, q.v);
+      q = c;
+      m = cq;
+    } else {
+      acc.store1(p.k, p.v);
+      p = c;
+      m = cp;
+    }
     c = cn;
     w = wn;
   }
@@ -840,26 +828,29 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
       dst[3][k] = stage[3 * L + k];
     }
   } else {
-    // double values out of compensated float slots: every thread converts its
-    // own slots in place once, then two components per staging round
-    if (t < nrows) {
-#pragma unroll 4
-      for (int q = 0; q < len; ++q) acc.finalize_inplace(q * R + t, kg);
-    }
+    // double values out of compensated float slots, two components per
+    // staging round: every thread stages its own row's (leading, error) pairs
+    // in CSR order, then the block converts them while streaming them out
+    // coalesced (the conversions spread evenly over the threads)
+    float2* pairs = reinterpret_cast<float2*>(smem + lay.nb0());
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       if (t < nrows) {
 #pragma unroll 4
         for (int q = 0; q < len; ++q) {
-          const double2 v = acc.finished(q * R + t, half);
-          stage[lb + q] = v.x;
-          stage[L + lb + q] = v.y;
+          const float4 pr = acc.pairs(q * R + t, half, kg);
+          pairs[lb + q] = make_float2(pr.x, pr.y);
+          pairs[L + lb + q] = make_float2(pr.z, pr.w);
         }
       }
       __syncthreads();
+      // half 0: G_x, G_y; half 1: G_z, A
+      Out* d0 = half ? dst[3] : dst[1];
+      Out* d1 = half ? dst[0] : dst[2];
       for (int k = t; k < L; k += R) {
-        dst[2 * half][k] = stage[k];
-        dst[2 * half + 1][k] = stage[L + k];
+        const float2 a = pairs[k], b = pairs[L + k];
+        d0[k] = pair_double(a.x, a.y);
+        d1[k] = pair_double(b.x, b.y);
       }
       if (half == 0) __syncthreads();
     }
