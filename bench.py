@@ -38,6 +38,8 @@ WORKLOADS = {
     "adjoint50": "Kuhn cube 50^3 hexes, 750,000 tets, jitter 15% h: vector-Jacobian product of R = A(u)u - b",
     "cube100": "Kuhn cube 100^3 hexes, 6,000,000 tets, 1,030,301 nodes, jitter 15% h, random numbering, seed 1",
     "cube8": "Kuhn cube 8^3 hexes, 3,072 tets, 729 nodes, natural numbering, seed 0",
+    "cube70": "Kuhn cube 70^3 hexes, 2,058,000 tets, 357,911 nodes, jitter 15% h, random numbering, seed 1 "
+              "(profiling case: the 100^3 recipe with outputs still above L2)",
     "cube200_rcm": "Kuhn cube 200^3 hexes, 48,000,000 tets, 8,120,601 nodes, jitter 15% h, RCM numbering, 5% noise",
     "cube200_random": "Kuhn cube 200^3 hexes, 48,000,000 tets, 8,120,601 nodes, jitter 15% h, random numbering, 5% noise",
 }

@@ -169,6 +169,7 @@ CONFIGS = {
     # name: (N, jitter, numbering, seed)
     "cube8": dict(N=8, jitter=0.0, numbering="natural", seed=0),
     "cube100": dict(N=100, jitter=0.15, numbering="random", seed=1),
+    "cube70": dict(N=70, jitter=0.15, numbering="random", seed=1),  # the cube100 recipe, smaller (profiling)
     "cube200_rcm": dict(N=200, jitter=0.15, numbering="rcm", seed=2, noise=0.05),
     "cube200_random": dict(N=200, jitter=0.15, numbering="random", seed=2, noise=0.05),
     "cube50": dict(N=50, jitter=0.15, numbering="natural", seed=4),

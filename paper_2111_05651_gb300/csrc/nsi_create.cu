@@ -557,12 +557,13 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   // 7. gather launch plan: largest rows-per-block whose entries fit the budget
   {
     // rows per block chosen for the most resident warps per SM (shared memory
-    // of the block's layout, the kernel's registers, 2048 threads per SM)
+    // of the block's layout, the kernel's registers, 2048 threads per SM); on
+    // a tie the smallest block, whose barriers hold fewer warps
     const size_t smem_sm = 228 * 1024, smem_max = 200 * 1024;
     const int regs = std::max(32, gather_kernel_regs(h->precision));
     const int W = std::max(1, (int)max_row);
     int chosen = 0, chosen_L = 0, chosen_S = 0, best_warps = 0;
-    for (int R : {128, 96, 64, 32}) {
+    for (int R : {32, 64, 96, 128}) {
       if (!h->gather_ok) break;
       int64_t mL = 0, mS = 0;
       for (int64_t r0 = 0; r0 < n; r0 += R) {
@@ -570,8 +571,9 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
         mL = std::max<int64_t>(mL, rp64[r1] - rp64[r0]);
         mS = std::max<int64_t>(mS, walk_ptr[r1] - walk_ptr[r0]);
       }
-      const size_t sm = gather_smem(h->precision, R, W, (int)mL, (int)mS).total();
-      if (sm > smem_max) continue;
+      const GatherSmem g = gather_smem(h->precision, R, W, (int)mL, (int)mS);
+      const size_t sm = g.total();
+      if (sm > smem_max || !g.stage_fits()) continue;
       int blocks = (int)std::min<size_t>({smem_sm / (sm + 1024), (size_t)32, (size_t)(2048 / R),
                                           (size_t)(65536 / (R * regs))});
       const int warps = blocks * R / 32;

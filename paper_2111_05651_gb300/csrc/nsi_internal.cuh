@@ -78,21 +78,25 @@ struct GatherPlan {
 //   nb0   T[4] per slot: edge vector d = x_j - x_i and u_x of the neighbour
 //   nb1   T[2] per slot: u_y, u_z
 //   acc   accumulators per slot (ab bytes): A and the three sums of c_i
-//   col   int32 per CSR entry; walk one byte per step (copied as aligned
-//         4-byte words, so S + 8 bytes)
+//   col   int32 per CSR entry, read only while the records are gathered: it
+//         shares nb1's bytes (nb1 is written after a barrier)
+//   walk  one byte per step (copied as aligned 4-byte words, so S + 8 bytes)
 // After the element loop, nb0 is reused to stage the finished values in CSR
 // order for the coalesced write-out.
 // Used identically by the host (launch size) and the kernel (carving).
 struct GatherSmem {
-  int R, W, L, S, tb, ab;
+  int R, W, L, S, tb, ab, ob, cr;  // ob: bytes of an output value; cr: components staged per write-out round
   __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ size_t N() const { return (size_t)R * W; }
   __host__ __device__ size_t nb0() const { return 0; }
   __host__ __device__ size_t nb1() const { return up16(nb0() + (size_t)4 * tb * N()); }
   __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
-  __host__ __device__ size_t col() const { return up16(acc() + (size_t)ab * N()); }
-  __host__ __device__ size_t walk() const { return up16(col() + (size_t)4 * L); }
+  __host__ __device__ size_t col() const { return nb1(); }  // (L <= N: 4 L bytes fit in nb1)
+  __host__ __device__ size_t walk() const { return up16(acc() + (size_t)ab * N()); }
   __host__ __device__ size_t total() const { return up16(walk() + (size_t)S + 8); }
+  // the write-out stages cr components of the block's L entries in nb0
+  __host__ __device__ size_t stage_bytes() const { return (size_t)cr * L * ob; }
+  __host__ __device__ bool stage_fits() const { return stage_bytes() <= nb1() - nb0(); }
 };
 
 __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S) {
@@ -103,6 +107,8 @@ __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, i
   g.S = S;
   g.tb = precision == NSI_FP64 ? 8 : 4;
   g.ab = precision == NSI_MIXED_F32_ACC32 ? 16 : 32;
+  g.ob = precision == NSI_MIXED_F32_ACC32 ? 4 : 8;
+  g.cr = precision == NSI_MIXED_F32_ACC64 ? 2 : 4;
   return g;
 }
 

@@ -584,6 +584,7 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   V3<T> m{T(0), T(0), T(0)};
   unsigned w = st[0];
   Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
+#pragma unroll 2  // two steps' arithmetic interleave (measured faster)
   for (int s = 0; s < nsteps; ++s) {
     // the next step's node, in flight while this element is evaluated (never
     // one of p, q, c: the walk is encoded that way; the last step reloads its
@@ -717,9 +718,14 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
         cp_async16(staged_half<P>(smem, lay, k, 0), r + 16);
       }
     }
+  }
+  // every row's column indices have been read: nb1, which holds them, may now
+  // be written
+  __syncthreads();
+  if (t < nrows) {
     cp_async_wait_all();
     // edge vectors d = x_j - x_i; the row's own record (its diagonal slot)
-    // gives the origin.  The slots are this thread's own: no barrier needed.
+    // gives the origin.  The slots are this thread's own.
     if (len > 0) {
       const int kd = dp * R + t;
       if constexpr (P == NSI_FP64) {
@@ -1506,7 +1512,8 @@ static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const Nsi
   if (st) return st;
   const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_steps);
   const size_t smem = lay.total();
-  if (smem > 200 * 1024) return fail(NSI_ERR_UNSUPPORTED, "batched meshes need more shared memory than a block has");
+  if (smem > 200 * 1024 || !lay.stage_fits())
+    return fail(NSI_ERR_UNSUPPORTED, "batched meshes need more shared memory than a block has");
   int per_sm = 0, sms = 0, dev = 0;
   NSI_CUDA(cudaGetDevice(&dev));
   NSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
