@@ -51,6 +51,9 @@ def _load():
             lib.oracle_element_batch.argtypes = [ctypes.c_int64, _d, _i32, _d, _d, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, _i64, ctypes.c_int64,
                                                  _d, _d, _d, _d, _d]
+            lib.oracle_nodal.restype = ctypes.c_int
+            lib.oracle_nodal.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, ctypes.c_double,
+                                         ctypes.c_double, _d, _d, _d]
             lib.oracle_pattern.restype = ctypes.c_int64
             lib.oracle_pattern.argtypes = [ctypes.c_int64, ctypes.c_int64, _i32, _i32, _i32]
             lib.oracle_assemble.restype = ctypes.c_int
@@ -146,6 +149,20 @@ def assemble_rows(coord, lnods, u, rows, un=None, rho=1.0, mu=1e-3, dt=1e-2, max
         raise ValueError(f"oracle_assemble_rows failed ({rc})")
     return [(cols[t, :count[t]].copy(), A[t, :count[t]].copy(), G[t, :, :count[t]].copy(), rhs[t].copy())
             for t in range(m)]
+
+
+def nodal(coord, lnods, un, rho=1.0, dt=1e-2):
+    """Nodal outputs of the paper's assembly (perform_assembly_in_global_system,
+    Listing 2): (rhsid [3, n], dt_rho [n], mass_rho [n]); see ``oracle_nodal``."""
+    lib = _load()
+    coord, lnods, un = _f64(coord), _ln(lnods), _f64(un)
+    n = coord.shape[0]
+    rhs = np.empty((3, n)); dtr = np.empty(n); mr = np.empty(n)
+    rc = lib.oracle_nodal(n, lnods.shape[0], _p(coord, _d), _p(lnods, _i32), _p(un, _d), rho, dt,
+                          _p(rhs, _d), _p(dtr, _d), _p(mr, _d))
+    if rc != 0:
+        raise ValueError(f"oracle_nodal failed ({rc})")
+    return rhs, dtr, mr
 
 
 def vjp(coord, lnods, u, w, rho=1.0, mu=1e-3, dt=1e-2):

@@ -196,6 +196,46 @@ int oracle_element_batch(int64_t n, const double* coord, const int32_t* lnods, c
     return 0;
 }
 
+/*
+ * Nodal outputs of perform_assembly_in_global_system (Listing 2), the paper's
+ * own kernel outputs: for every element, in increasing element order, and
+ * every node a of it,
+ *   rhsid[k][lnods[a]]  += elrbu[k][a]   = rho/dt (sum_g gpvol[g] N_a(xi_g)) un[a][k]
+ *   dt_rho[lnods[a]]    += eldtrho[a]    = rho/dt  sum_g gpvol[g] N_a(xi_g)
+ *   mass_rho[lnods[a]]  += elmurho[a]    = rho     sum_g gpvol[g] N_a(xi_g)
+ * The paper prints the accumulation, not the element values: eldtrho and
+ * elmurho are read as the row-sum lumped density mass over dt and the lumped
+ * density mass (the same lumping as the matrix diagonal and the RHS).
+ * rhs is [3][n]; dt_rho and mass_rho are [n].
+ */
+int oracle_nodal(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* un,
+                 double rho, double dt, double* rhs, double* dt_rho, double* mass_rho) {
+    double shape[PGAUS][PNODE], weight[PGAUS];
+    gauss_rule(shape, weight);
+    memset(rhs, 0, sizeof(double) * 3 * n);
+    memset(dt_rho, 0, sizeof(double) * n);
+    memset(mass_rho, 0, sizeof(double) * n);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        for (int a = 0; a < PNODE; ++a)
+            if (ln[a] < 0 || ln[a] >= n) return -1;
+        double X[PNODE][NDIME], Un[PNODE][NDIME];
+        gather(coord, un, un, ln, X, Un, Un);
+        double gpcar[PNODE][NDIME];
+        const double detjac = cartesian_derivatives(X, gpcar);
+        if (!(detjac > 0.0)) return -2;
+        for (int a = 0; a < PNODE; ++a) {
+            double lump = 0.0;
+            for (int g = 0; g < PGAUS; ++g) lump += weight[g] * detjac * shape[g][a];
+            const double eldtrho = rho * lump / dt, elmurho = rho * lump;
+            for (int k = 0; k < NDIME; ++k) rhs[k * n + ln[a]] += rho * lump * Un[a][k] / dt;
+            dt_rho[ln[a]] += eldtrho;
+            mass_rho[ln[a]] += elmurho;
+        }
+    }
+    return 0;
+}
+
 static int cmp_i64(const void* x, const void* y) {
     int64_t a = *(const int64_t*)x, c = *(const int64_t*)y;
     return (a > c) - (a < c);

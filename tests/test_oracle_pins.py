@@ -283,6 +283,30 @@ def test_rhs_totals():
     np.testing.assert_allclose(rhs_c.sum(axis=1), rho * np.array([0.5, 1.5, -2.0]) / dt, rtol=1e-12)
 
 
+def test_nodal_outputs_closed_forms():
+    """The paper's nodal outputs (rhsid, dt_rho, mass_rho of Listing 2).
+
+    Unjittered Kuhn cube: every tet has volume h^3/6, so node i receives
+    rho h^3/24 per incident tet (counted from the connectivity, no geometry);
+    mass_rho sums to rho times the cube's volume on any mesh; dt_rho is
+    mass_rho / dt; rhsid is the lumped dt_rho u^n and equals the RHS of the
+    matrix assembly.  A wrong lumping factor, a missing rho or dt, or a
+    transposed rhs layout fails one of these."""
+    N, rho, dt = 4, 1.7, 0.02
+    mesh, u = _mesh(N, 0.0, "random", seed=3)
+    rhs, dtr, mr = oracle.nodal(mesh.coord, mesh.lnods, u, rho=rho, dt=dt)
+    count = np.bincount(mesh.lnods.ravel(), minlength=mesh.n_nodes)
+    np.testing.assert_allclose(mr, rho * count / (24.0 * N ** 3), rtol=1e-13)
+    assert mr.sum() == pytest.approx(rho, rel=1e-13)
+    np.testing.assert_allclose(dtr, mr / dt, rtol=1e-13)
+    np.testing.assert_allclose(rhs, dtr[None, :] * u.T, rtol=1e-13, atol=1e-13 * np.abs(rhs).max())
+    mesh, u = _mesh(5, 0.15, "rcm", seed=4)
+    rhs, dtr, mr = oracle.nodal(mesh.coord, mesh.lnods, u, rho=rho, dt=dt)
+    assert mr.sum() == pytest.approx(rho, rel=1e-13)  # jitter keeps the unit cube's volume
+    _, _, _, _, rhs_a = oracle.assemble(mesh.coord, mesh.lnods, u, rho=rho, mu=1e-3, dt=dt)
+    np.testing.assert_allclose(rhs, rhs_a, rtol=1e-13, atol=1e-13 * np.abs(rhs_a).max())
+
+
 def test_separate_rhs_velocity():
     """u^n enters only the RHS; u only A."""
     mesh, u = _mesh(3, 0.1, "natural", seed=6)
