@@ -36,6 +36,8 @@ WORKLOADS = {
     "batch64": "64 jittered Kuhn cubes, N ~ U{10..60} hexes a side (seeded), one persistent batched launch "
                "captured with the velocity update in a CUDA graph and replayed every step",
     "adjoint50": "Kuhn cube 50^3 hexes, 750,000 tets, jitter 15% h: vector-Jacobian product of R = A(u)u - b",
+    "step100": "Kuhn cube 100^3 hexes, 6,000,000 tets, jitter 15% h, random numbering, seed 1: one time step with "
+               "cached geometry, A = A_static + C(u) and rhs (A_static and G assembled once, outside the timing)",
     "cube100": "Kuhn cube 100^3 hexes, 6,000,000 tets, 1,030,301 nodes, jitter 15% h, random numbering, seed 1",
     "cube8": "Kuhn cube 8^3 hexes, 3,072 tets, 729 nodes, natural numbering, seed 0",
     "cube70": "Kuhn cube 70^3 hexes, 2,058,000 tets, 357,911 nodes, jitter 15% h, random numbering, seed 1 "
@@ -353,13 +355,7 @@ def run_gpu(args, world, rank, local):
     kernel = {"gather": "fan_kernel" if args.fan else "gather_kernel", "atomic": "elem_kernel",
               "color": "elem_kernel"}[main["mode"]]
     bytes_alg = algorithmic_bytes(E, n, main["nnz"], main_prec)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = hbm_peak()
     achieved = bytes_alg / (main["kernel_ms"] * 1e-3) / 1e9
     line = {
         "metric": "tet elements assembled/s", "value": value, "unit": "elements/s", "n_gpus": world,
@@ -374,7 +370,7 @@ def run_gpu(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": read_traffic(kernel, args.workload, main_prec), "kernel": kernel,
                      "algorithmic_bytes": bytes_alg, "kernel_ms": main["kernel_ms"],
-                     "peak_source": peak_src + " hbm_gbs (copy, burst)"},
+                     "peak_source": peak_src},
         "clocks": main["clocks"],
         "gpu_launches": args.steps * main["launches_per_step"],
         "max_rel_err": main.get("max_rel_err"),
@@ -492,6 +488,78 @@ def run_adjoint(args, world, rank, local):
                           "modes": res}), flush=True)
 
 
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured hbm_gbs (copy, burst)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def step_bytes(E, n, nnz, precision):
+    """Compulsory HBM bytes of one cached-geometry step: connectivity, node data,
+    row_ptr + col_idx, A_static read and A written, rhs written."""
+    sx, su, so = PREC_BYTES[precision]
+    return 16 * E + n * (3 * sx + 3 * su) + 4 * (n + 1) + 4 * nnz + 2 * so * nnz + 3 * so * n
+
+
+def run_step(args, world, rank, local):
+    import torch
+
+    import oracle
+    import paper_2111_05651_gb300 as nsi
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nsi.load_library()
+    mesh, u = meshgen.config_mesh("cube100")
+    E, n = mesh.n_elems, mesh.n_nodes
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(9).integers(0, n, 24)]))
+    res = {}
+    for prec in ("mixed64", "mixed32", "fp64"):
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec)
+        vt = torch.float64 if prec == "fp64" else torch.float32
+        ut = torch.as_tensor(u.T.copy()).to(dev, vt).contiguous()
+        A_static, _ = asm.static_part(rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
+        out = (torch.empty_like(A_static), torch.empty(3, n, dtype=asm.out_dtype, device=dev))
+        fn = lambda: asm.assemble_convective(ut, A_static, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT,  # noqa
+                                             out=out)
+        steps = args.steps if prec == "mixed64" else max(3, min(args.steps, 20))
+        t_step, t_kern = time_steps(asm, fn, steps, args.warmup, lambda: flush_buf.fill_(1), stream)
+        ms, kms = float(np.mean(t_step)), float(np.mean(t_kern))
+        # sampled rows of A and rhs against the oracle's full assembly
+        u_in = u if prec == "fp64" else u.astype(np.float32).astype(np.float64)
+        ref = oracle.assemble_rows(mesh.coord, mesh.lnods, u_in, rows, None, meshgen.RHO, meshgen.MU, meshgen.DT)
+        rp = asm.pattern()[0].cpu().numpy()
+        Ah, rh = out[0].double().cpu().numpy(), out[1].double().cpu().numpy()
+        err = 0.0
+        for r, (cols, a, g, orh) in zip(rows, ref):
+            err = max(err, np.abs(Ah[rp[r]:rp[r + 1]] - a).max() / np.abs(a).max(),
+                      np.abs(rh[:, r] - orh).max() / np.abs(rh).max())
+        nb = step_bytes(E, n, asm.nnz, prec)
+        res[prec] = {"ms": ms, "kernel_ms": kms, "elements_per_s": E / (ms * 1e-3), "max_rel_err": float(err),
+                     "algorithmic_bytes": nb, "achieved_gbs": nb / (kms * 1e-3) / 1e9}
+        asm.close()
+    ms = allreduce_max(res["mixed64"]["ms"], world)
+    if rank == 0:
+        peak, src = hbm_peak()
+        m = res["mixed64"]
+        print(json.dumps({"metric": "tet elements stepped/s (cached-geometry convective step)",
+                          "value": world * E / (ms * 1e-3), "unit": "elements/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "dtype": "f32 (f64 output)", "data": "synthetic",
+                          "config": {"workload": WORKLOADS["step100"], "precision": "mixed64",
+                                     "l2": "flushed (256 MiB write) before every timed step"},
+                          "roofline": {"bound": "hbm", "achieved": m["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                                       "frac": m["achieved_gbs"] / peak, "traffic": None, "kernel": "step_kernel",
+                                       "algorithmic_bytes": m["algorithmic_bytes"], "kernel_ms": m["kernel_ms"],
+                                       "peak_source": src},
+                          "max_rel_err": m["max_rel_err"], "modes": res}), flush=True)
+
+
 def run_profile(args):
     """Untimed assemblies for an external profiler: per precision, 3 calls."""
     import torch
@@ -545,6 +613,8 @@ def main():
             run_batch(args, world, rank, local)
         elif args.workload == "adjoint50":
             run_adjoint(args, world, rank, local)
+        elif args.workload == "step100":
+            run_step(args, world, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:

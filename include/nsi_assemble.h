@@ -185,6 +185,37 @@ nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const
                                 int32_t count, void* stream);
 
 /*
+ * One time step with cached geometry.  Over time steps on a fixed mesh with
+ * fixed rho, mu and dt (Alya assembles every step, Section II), only the
+ * convection and the RHS of the assembly depend on the velocity:
+ *   A_val = A_static + C(u),  rhs = lumped rho u^n / dt  (as nsi_assemble),
+ * where A_static is the A of nsi_assemble at u = 0 with the same rho, mu and
+ * dt (the viscous part plus the lumped mass) and C(u) the convection term.  G
+ * does not change and is not written.  A_static, A_val: device [nnz] of the
+ * handle's output type (A_val may alias A_static: every entry is read before
+ * it is written, by the same thread); rhs: device [3][n_nodes], overwritten;
+ * the velocities in `f` as for nsi_assemble.  Needs the row-gather map
+ * (rows of at most 32 entries): NSI_ERR_UNSUPPORTED otherwise.
+ */
+nsi_status nsi_assemble_convective(NsiHandle* h, const NsiFields* f, const void* A_static, void* A_val,
+                                   void* rhs, void* stream);
+
+/*
+ * The per-node outputs of the paper's assembly kernel
+ * (perform_assembly_in_global_system, Listing 2), without the matrix:
+ *   rhs[k][i]   = sum over elements e of i of rho |T_e| u^n_i[k] / (4 dt)  (rhsid)
+ *   dt_rho[i]   = sum over elements e of i of rho |T_e| / (4 dt)           (dt_rho_nsi)
+ *   mass_rho[i] = sum over elements e of i of rho |T_e| / 4                (mass_rho_nsi)
+ * (the paper prints the accumulation, not the element values: read as the
+ * row-sum lumped density mass over dt and the lumped density mass).  rhs:
+ * device [3][n_nodes], dt_rho and mass_rho device [n_nodes], all of the
+ * handle's output type and overwritten; u^n is f->u_n (or f->u).  Needs the
+ * row-gather map: NSI_ERR_UNSUPPORTED otherwise.
+ */
+nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void* dt_rho, void* mass_rho,
+                              void* stream);
+
+/*
  * Vector-Jacobian product of the assembled residual R(u, mu) = A(u) u - b
  * (b held fixed):  grad_u[l][m] = sum_{i,k} w[k][i] dR[k][i]/du[l][m] and
  * grad_mu = sum_{i,k} w[k][i] dR[k][i]/dmu.  Element geometry is recomputed

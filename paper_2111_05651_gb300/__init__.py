@@ -28,6 +28,7 @@ __all__ = [
     "load_library", "library_path", "exported_symbols",
     "nsi_assemble_create", "nsi_assemble_destroy", "nsi_csr_pattern", "nsi_csr_pattern_copy", "nsi_info",
     "nsi_assemble", "nsi_assemble_mode", "nsi_assemble_batched", "nsi_assemble_vjp", "nsi_assemble_host",
+    "nsi_assemble_convective", "nsi_assemble_nodal",
     "nsi_residual", "nsi_device_status", "nsi_set_timing_events", "nsi_autotune", "nsi_set_launch",
     "nsi_last_error", "nsi_abi_version",
     "Assembler", "NsiResidual", "assemble_batched",
@@ -91,6 +92,8 @@ _SIGNATURES = {
     "nsi_assemble_batched": [ctypes.POINTER(_P), ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs),
                              ctypes.c_int32, _P],
     "nsi_assemble_vjp": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
+    "nsi_assemble_convective": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
+    "nsi_assemble_nodal": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
     "nsi_assemble_host": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), _P],
     "nsi_residual": [_P, ctypes.POINTER(NsiFields), _P, _P],
     "nsi_device_status": [_P, _P],
@@ -193,6 +196,14 @@ def nsi_assemble_batched(handles, fields, outputs, stream=None):
 
 def nsi_assemble_vjp(h, fields: NsiFields, w_ptr, grad_u_ptr, grad_mu_ptr, stream=None):
     _check(load_library().nsi_assemble_vjp(h, ctypes.byref(fields), w_ptr, grad_u_ptr, grad_mu_ptr, stream))
+
+
+def nsi_assemble_convective(h, fields: NsiFields, A_static_ptr, A_ptr, rhs_ptr, stream=None):
+    _check(load_library().nsi_assemble_convective(h, ctypes.byref(fields), A_static_ptr, A_ptr, rhs_ptr, stream))
+
+
+def nsi_assemble_nodal(h, fields: NsiFields, rhs_ptr, dt_rho_ptr, mass_rho_ptr, stream=None):
+    _check(load_library().nsi_assemble_nodal(h, ctypes.byref(fields), rhs_ptr, dt_rho_ptr, mass_rho_ptr, stream))
 
 
 def nsi_assemble_host(h, fields: NsiFields, outputs: NsiOutputs, stream=None):
@@ -342,6 +353,39 @@ class Assembler:
         mode = self.scatter if scatter is None else (SCATTERS[scatter] if isinstance(scatter, str) else scatter)
         nsi_assemble_mode(self.handle, f, o, mode, _stream_ptr(stream))
         return A, G, rhs
+
+    def static_part(self, rho=1.0, mu=1e-3, dt=1e-2, out=None, stream=None):
+        """(A_static, G): the velocity-independent assembly (A at u = 0: the viscous
+        part plus the lumped mass; G), for ``assemble_convective``."""
+        torch = _torch()
+        zero = torch.zeros(3, self.n, dtype=self.vel_dtype, device=self.device)
+        A, G, _ = self.assemble(zero, rho=rho, mu=mu, dt=dt, out=out, stream=stream)
+        return A, G
+
+    def assemble_convective(self, u, A_static, u_n=None, rho=1.0, mu=1e-3, dt=1e-2, out=None, stream=None):
+        """(A, rhs) of one time step with cached geometry: A = A_static + C(u)."""
+        torch = _torch()
+        f, keep = self.fields(u, u_n, rho, mu, dt)
+        if out is None:
+            out = (torch.empty(self.nnz, dtype=self.out_dtype, device=self.device),
+                   torch.empty(3, self.n, dtype=self.out_dtype, device=self.device))
+        A, rhs = out
+        if A_static.dtype != self.out_dtype or A_static.numel() != self.nnz or not A_static.is_contiguous():
+            raise ValueError("A_static must be a contiguous [nnz] tensor of the output dtype")
+        nsi_assemble_convective(self.handle, f, _ptr(A_static), _ptr(A), _ptr(rhs), _stream_ptr(stream))
+        return A, rhs
+
+    def nodal(self, u_n, rho=1.0, dt=1e-2, out=None, stream=None):
+        """(rhs [3, n], dt_rho [n], mass_rho [n]): the paper's per-node outputs."""
+        torch = _torch()
+        f, keep = self.fields(u_n, None, rho, 0.0, dt)
+        if out is None:
+            out = (torch.empty(3, self.n, dtype=self.out_dtype, device=self.device),
+                   torch.empty(self.n, dtype=self.out_dtype, device=self.device),
+                   torch.empty(self.n, dtype=self.out_dtype, device=self.device))
+        rhs, dtr, mr = out
+        nsi_assemble_nodal(self.handle, f, _ptr(rhs), _ptr(dtr), _ptr(mr), _stream_ptr(stream))
+        return rhs, dtr, mr
 
     def assemble_host(self, u_host, A_host, G_host, rhs_host, rho=1.0, mu=1e-3, dt=1e-2, stream=None):
         """End-to-end call on HOST tensors (pinned recommended): H2D of u, assembly, D2H of outputs."""

@@ -99,7 +99,9 @@ struct GatherSmem {
   __host__ __device__ bool stage_fits() const { return stage_bytes() <= nb1() - nb0(); }
 };
 
-__host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S) {
+// step: the layout of the time-step kernels (one accumulator per slot, at the
+// 16-byte stride of the staged record halves; FP64 two planes of 16)
+__host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, int L, int S, bool step = false) {
   GatherSmem g;
   g.R = R;
   g.W = W;
@@ -107,6 +109,7 @@ __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, i
   g.S = S;
   g.tb = precision == NSI_FP64 ? 8 : 4;
   g.ab = precision == NSI_MIXED_F32_ACC32 ? 16 : 32;
+  if (step) g.ab = precision == NSI_FP64 ? 32 : 16;
   g.ob = precision == NSI_MIXED_F32_ACC32 ? 4 : 8;
   g.cr = precision == NSI_MIXED_F32_ACC64 ? 2 : 4;
   return g;

@@ -640,12 +640,26 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   acc.store1(q.k, q.v);
 }
 
-// one block of rows [r0, r0 + blockDim.x) of one mesh
-template <int P, bool DEBUG>
-__device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& f, const OutView& o, int64_t r0,
-                                            unsigned char* smem, const GatherSmem& lay) {
+// Per-thread view of one block of rows [r0, r0 + blockDim.x) of one mesh.
+template <typename T>
+struct BlockRows {
+  int R, t, nrows, L, len, lb, s0, s1, dp;
+  int64_t i;
+  int32_t base;
+  V3<T> uni;
+};
+
+// Phases 0 and 1 of a row-gather block, shared by the full assembly and the
+// time-step kernels: the row's scalars; the block's column indices and walk
+// steps (asynchronous copies); every neighbour's record (calculate_transients
+// for the row, asynchronous copies all in flight at once), turned into edge
+// vectors d = x_j - x_i (the row's own record, its diagonal slot, gives the
+// origin) and velocities in nb0/nb1; the accumulators zeroed.  Returns false
+// (block-uniform) if the block does not fit the layout.
+template <int P, bool DEBUG, typename Accum>
+__device__ __forceinline__ bool stage_block(const MeshView& m, const FieldView& f, int64_t r0, unsigned char* smem,
+                                            const GatherSmem& lay, Accum& acc, BlockRows<typename Prec<P>::T>& b) {
   using T = typename Prec<P>::T;
-  using Out = typename Prec<P>::Out;
   const int R = blockDim.x;
   const int t = threadIdx.x;
   const int64_t r_end = min(r0 + (int64_t)R, m.n);
@@ -656,17 +670,12 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
   const int S = send - sbase;
   if (DEBUG && (L > lay.L || S > lay.S || R != lay.R)) {
     if (t == 0) atomicOr(m.err, ERR_STAR);
-    return;
+    return false;
   }
   T4<T>* __restrict__ nb0 = reinterpret_cast<T4<T>*>(smem + lay.nb0());
   T2<T>* __restrict__ nb1 = reinterpret_cast<T2<T>*>(smem + lay.nb1());
-  AccSmem<P> acc(smem + lay.acc(), lay.N());
   int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
   uint8_t* walk = smem + lay.walk();
-  const T kc = kc_of<T>(f);
-  const T kmu = kmu_of<T>(f);
-  const T kmass = kmass_of<T>(f);
-  const T kg = (T)(-1.0 / 24.0);
 
   // phase 0: the row's scalars; the block's column indices and walk steps by
   // asynchronous copies (all in flight)
@@ -694,8 +703,6 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
 
   const int len = re - rs;
   const int lb = rs - base;
-  Acc<P> detsum;
-  detsum.zero();
   if (t < nrows) {
     // phase 1 (calculate_transients for the row): every neighbour's record,
     // by asynchronous copies all in flight at once
@@ -754,6 +761,34 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
         }
       }
     }
+  }
+  b = BlockRows<T>{R, t, nrows, L, len, lb, s0, s1, dp, i, base, uni};
+  return true;
+}
+
+// one block of rows [r0, r0 + blockDim.x) of one mesh
+template <int P, bool DEBUG>
+__device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& f, const OutView& o, int64_t r0,
+                                            unsigned char* smem, const GatherSmem& lay) {
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  AccSmem<P> acc(smem + lay.acc(), lay.N());
+  BlockRows<T> b;
+  if (!stage_block<P, DEBUG>(m, f, r0, smem, lay, acc, b)) return;
+  const int R = b.R, t = b.t, nrows = b.nrows, L = b.L, len = b.len, lb = b.lb, s0 = b.s0, s1 = b.s1, dp = b.dp;
+  const int64_t i = b.i;
+  const int32_t base = b.base;
+  const V3<T> uni = b.uni;
+  const T4<T>* __restrict__ nb0 = reinterpret_cast<const T4<T>*>(smem + lay.nb0());
+  const T2<T>* __restrict__ nb1 = reinterpret_cast<const T2<T>*>(smem + lay.nb1());
+  const uint8_t* walk = smem + lay.walk();
+  const T kc = kc_of<T>(f);
+  const T kmu = kmu_of<T>(f);
+  const T kmass = kmass_of<T>(f);
+  const T kg = (T)(-1.0 / 24.0);
+  Acc<P> detsum;
+  detsum.zero();
+  if (t < nrows) {
     // phase 2: every element of the row's star, accumulated privately
     if (len > 0) {
       if (DEBUG && dp >= len) atomicOr(m.err, ERR_STAR);
@@ -861,6 +896,259 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
       if (half == 0) __syncthreads();
     }
   }
+}
+
+// ------------------------------------------- cached-geometry time step ---
+// Over time steps on a fixed mesh with fixed rho, mu and dt, the viscous
+// part, the lumped mass and the pressure gradient of the assembly do not
+// change; only the convection C(u) and the RHS do.  The step kernel forms
+//   A = A_static + C(u),  C(i,x) = sum over the star of i of w_e . c_x,
+//   w_e = rho/120 (2 u_i + u_p + u_q + u_c)
+// and the lumped RHS, where A_static is the A of a full assembly at u = 0
+// (the viscous part and the lumped mass).  C has zero row sums (the shape
+// gradients of an element sum to zero), so C(i,i) = -sum_{j != i} C(i,j).  G
+// is not touched.  The nodal variant forms the paper's per-node outputs
+// instead (perform_assembly_in_global_system): rhsid, dt_rho = sum_e
+// rho|T|/(4 dt) and mass_rho = sum_e rho|T|/4.  Both follow the element walk
+// of the full assembly, with one accumulator per slot (none for the nodal
+// outputs).
+
+// A-only accumulator slots, at the stride of the staged record halves (16
+// bytes, FP64 two planes of 16): a slot's bytes first receive its record's
+// second half, then its accumulator.
+template <int P>
+struct AccA;
+template <>
+struct AccA<NSI_MIXED_F32_ACC32> {
+  float4* __restrict__ a;
+  using Slot = float;
+  __device__ __forceinline__ AccA(unsigned char* p) : a(reinterpret_cast<float4*>(p)) {}
+  __device__ __forceinline__ void zero(int k) { a[k].x = 0.f; }
+  __device__ __forceinline__ Slot load1(int k) const { return a[k].x; }
+  __device__ __forceinline__ void store1(int k, Slot v) { a[k].x = v; }
+  static __device__ __forceinline__ void add(Slot& s, float x) { s += x; }
+  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>& r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R)
+      if (k != kd) r.add(a[k].x);
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>& r) { a[k].x = r.v; }
+};
+template <>
+struct AccA<NSI_MIXED_F32_ACC64> {
+  float4* __restrict__ a;
+  using Slot = float2;  // leading part, error term
+  __device__ __forceinline__ AccA(unsigned char* p) : a(reinterpret_cast<float4*>(p)) {}
+  __device__ __forceinline__ void zero(int k) { a[k].x = a[k].y = 0.f; }
+  __device__ __forceinline__ Slot load1(int k) const {
+    const float4 v = a[k];
+    return make_float2(v.x, v.y);
+  }
+  __device__ __forceinline__ void store1(int k, Slot v) { reinterpret_cast<float2*>(a + k)[0] = v; }
+  static __device__ __forceinline__ void add(Slot& s, float x) {
+    float sum, e;
+    two_sum(s.x, x, sum, e);
+    s.x = sum;
+    s.y += e;
+  }
+  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>& r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R)
+      if (k != kd) {
+        const float4 v = a[k];
+        r.add(v.x);
+        r.lo += v.y;
+      }
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>& r) {
+    reinterpret_cast<float2*>(a + k)[0] = make_float2(r.hi, r.lo);
+  }
+};
+template <>
+struct AccA<NSI_FP64> {
+  T2<double>* __restrict__ a;  // plane 0 of the staged halves
+  using Slot = double;
+  __device__ __forceinline__ AccA(unsigned char* p) : a(reinterpret_cast<T2<double>*>(p)) {}
+  __device__ __forceinline__ void zero(int k) { a[k].x = 0.0; }
+  __device__ __forceinline__ Slot load1(int k) const { return a[k].x; }
+  __device__ __forceinline__ void store1(int k, Slot v) { a[k].x = v; }
+  static __device__ __forceinline__ void add(Slot& s, double x) { s += x; }
+  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_FP64>& r) const {
+    for (int q = 0, k = t; q < len; ++q, k += R)
+      if (k != kd) r.add(a[k].x);
+  }
+  __device__ __forceinline__ void set(int k, const Acc<NSI_FP64>& r) { a[k].x = r.v; }
+};
+
+// The element walk of the time step: det for the lumped sums and, unless
+// NODAL, the convection w . c_x into the window's accumulators.  Same window,
+// orientation and carried cofactor as walk_row.
+template <int P, bool NODAL, bool DEBUG>
+__device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int nsteps, int len, int kd,
+                                          const T4<typename Prec<P>::T>* __restrict__ nb0,
+                                          const T2<typename Prec<P>::T>* __restrict__ nb1, AccA<P>& acc, int t,
+                                          int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
+                                          Acc<P>& detsum, unsigned* err) {
+  using T = typename Prec<P>::T;
+  using Node = WalkNode<T, typename AccA<P>::Slot>;
+  if (nsteps <= 0) return;
+  if (DEBUG) {
+    bool ok = true;
+    for (int s = 0; s < nsteps; ++s) ok &= (int)(st[s] & WALK_POS) < len;
+    if (!ok) {
+      atomicOr(err, ERR_STAR);
+      return;
+    }
+  }
+  auto load = [&](int k) {
+    const T4<T> a = nb0[k];
+    Node nd;
+    nd.k = k;
+    nd.d = V3<T>{a.x, a.y, a.z};
+    if constexpr (!NODAL) {
+      const T2<T> b = nb1[k];
+      nd.u = V3<T>{a.w, b.x, b.y};
+      nd.v = acc.load1(k);
+    }
+    return nd;
+  };
+  const int last = nsteps - 1;
+  Node p = load(kd);
+  Node q = p;
+  V3<T> m{T(0), T(0), T(0)};
+  unsigned w = st[0];
+  Node c = load((int)(w & WALK_POS) * R + t);
+#pragma unroll 2
+  for (int s = 0; s < nsteps; ++s) {
+    const unsigned wn = st[min(s + 1, last)];
+    const Node cn = load((int)(wn & WALK_POS) * R + t);
+    const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);
+    const bool elem = (w & WALK_ELEM) != 0u;
+    const T f = elem ? ((w & WALK_NEG) ? T(-1) : T(1)) : T(0);  // orientation, or 0
+    detsum.add(f * dot(p.d, cp));
+    if constexpr (!NODAL) {
+      const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x), kc * (u2i.y + p.u.y + q.u.y + c.u.y),
+                     kc * (u2i.z + p.u.z + q.u.z + c.u.z)};
+      AccA<P>::add(p.v, f * dot(w3, cp));
+      AccA<P>::add(q.v, f * dot(w3, cq));
+      AccA<P>::add(c.v, -f * dot(w3, m));
+    }
+    if (w & WALK_EVQ) {
+      if constexpr (!NODAL) acc.store1(q.k, q.v);
+      q = c;
+      m = cq;
+    } else {
+      if constexpr (!NODAL) acc.store1(p.k, p.v);
+      p = c;
+      m = cp;
+    }
+    c = cn;
+    w = wn;
+  }
+  if constexpr (!NODAL) {
+    acc.store1(p.k, p.v);
+    acc.store1(q.k, q.v);
+  }
+}
+
+// outputs of the time-step kernels; kmr = rho/24 (the density mass per det)
+struct StepView {
+  const void* A_static;
+  void* A;
+  void* rhs;
+  void* dt_rho;
+  void* mass_rho;
+  double kmr;
+  float kmrf;
+};
+
+template <typename T, int P>
+__device__ __forceinline__ Acc<P> scaled_sum(const Acc<P>& s, T c) {
+  Acc<P> r;
+  if constexpr (P == NSI_MIXED_F32_ACC64) {
+    const float p = s.hi * c;  // c * (hi + lo), product error kept
+    r.hi = p;
+    r.lo = fmaf(s.hi, c, -p) + s.lo * c;
+  } else {
+    r.v = s.v * c;
+  }
+  return r;
+}
+
+template <int P, bool NODAL, bool DEBUG>
+__device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f, const StepView& o, int64_t r0,
+                                          unsigned char* smem, const GatherSmem& lay) {
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  AccA<P> acc(smem + lay.acc());
+  BlockRows<T> b;
+  if (!stage_block<P, DEBUG>(m, f, r0, smem, lay, acc, b)) return;
+  const int R = b.R, t = b.t;
+  const T4<T>* __restrict__ nb0 = reinterpret_cast<const T4<T>*>(smem + lay.nb0());
+  const T2<T>* __restrict__ nb1 = reinterpret_cast<const T2<T>*>(smem + lay.nb1());
+  const T kc = kc_of<T>(f);
+  const T kmass = kmass_of<T>(f);
+  Acc<P> detsum;
+  detsum.zero();
+  if (t < b.nrows) {
+    const int kd = b.dp * R + t;
+    if (b.len > 0) {
+      if (DEBUG && b.dp >= b.len) atomicOr(m.err, ERR_STAR);
+      const T4<T> di = nb0[kd];
+      const T2<T> ei = nb1[kd];
+      const V3<T> u2i{di.w + di.w, ei.x + ei.x, ei.y + ei.y};
+      walk_step<P, NODAL, DEBUG>(smem + lay.walk() + b.s0, b.s1 - b.s0, b.len, kd, nb0, nb1, acc, t, R, u2i, kc,
+                                 detsum, m.err);
+      if constexpr (!NODAL) {  // C(i,i) = -sum_{j != i} C(i,j)
+        Acc<P> rsum;
+        rsum.zero();
+        acc.row_sum(t, R, b.len, kd, rsum);
+        Acc<P> dg;
+        if constexpr (P == NSI_MIXED_F32_ACC64) {
+          dg.hi = -rsum.hi;
+          dg.lo = -rsum.lo;
+        } else {
+          dg.v = -rsum.v;
+        }
+        if (!DEBUG || b.dp < b.len) acc.set(kd, dg);
+      }
+    }
+    // lumped RHS: (sum_e rho |T_e| / (4 dt)) u^n_i
+    const T unk[3] = {b.uni.x, b.uni.y, b.uni.z};
+    Out* Rh = static_cast<Out*>(o.rhs);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) store_acc(Rh + k * m.n + b.i, scaled_sum<T, P>(detsum, kmass * unk[k]));
+    if constexpr (NODAL) {
+      store_acc(static_cast<Out*>(o.dt_rho) + b.i, scaled_sum<T, P>(detsum, kmass));
+      store_acc(static_cast<Out*>(o.mass_rho) + b.i, scaled_sum<T, P>(detsum, (T)(sizeof(T) == 8 ? o.kmr : o.kmrf)));
+    }
+  }
+  if constexpr (!NODAL) {
+    __syncthreads();
+    // the block's contiguous slice of A: staged in CSR order, then
+    // A = A_static + C streamed out coalesced
+    const Out* As = static_cast<const Out*>(o.A_static) + b.base;
+    Out* A = static_cast<Out*>(o.A) + b.base;
+    if constexpr (P == NSI_MIXED_F32_ACC64) {
+      float2* stage = reinterpret_cast<float2*>(smem + lay.nb0());
+      if (t < b.nrows)
+        for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
+      __syncthreads();
+#pragma unroll 2
+      for (int k = t; k < b.L; k += R) A[k] = As[k] + pair_double(stage[k].x, stage[k].y);
+    } else {
+      Out* stage = reinterpret_cast<Out*>(smem + lay.nb0());
+      if (t < b.nrows)
+        for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
+      __syncthreads();
+#pragma unroll 2
+      for (int k = t; k < b.L; k += R) A[k] = As[k] + stage[k];
+    }
+  }
+}
+
+template <int P, bool NODAL, bool DEBUG>
+__global__ void __launch_bounds__(128) step_kernel(MeshView m, FieldView f, StepView o, GatherSmem lay) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_rows<P, NODAL, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, smem_raw, lay);
 }
 
 // ------------------------------------------------------ edge-fan kernel ---
@@ -1439,6 +1727,53 @@ static nsi_status assemble_dispatch(NsiHandle* h, const NsiFields* f, const NsiO
   }
 }
 
+// the time-step kernels (convective step, nodal outputs): pack, then one
+// step_kernel launch with the handle's rows per block
+template <int P, bool NODAL, bool DEBUG>
+static nsi_status set_step_smem() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(step_kernel<P, NODAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute(step smem)");
+  return NSI_OK;
+}
+
+template <int P, bool NODAL>
+static nsi_status step_p(NsiHandle* h, const FieldView& f, const StepView& o, cudaStream_t s) {
+  const MeshView m = view_of(h);
+  nsi_status st = h->debug ? set_step_smem<P, NODAL, true>() : set_step_smem<P, NODAL, false>();
+  if (st) return st;
+  const int R = h->plan.rows_per_block;
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps, true);
+  const size_t smem = lay.total();
+  if (smem > 200 * 1024) return fail(NSI_ERR_UNSUPPORTED, "the time-step layout needs more shared memory than a block has");
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, h->rec);
+  if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
+  if (h->debug) step_kernel<P, NODAL, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
+  else step_kernel<P, NODAL, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
+  if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
+  return check_launch("step_kernel");
+}
+
+static nsi_status step_dispatch(NsiHandle* h, const NsiFields* f, const StepView& o, bool nodal, cudaStream_t s) {
+  if (!h->gather_ok || h->n == 0)
+    return h->n == 0 ? NSI_OK : fail(NSI_ERR_UNSUPPORTED, "the time-step kernels need rows of at most 32 entries");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");
+  const FieldView fv = fields_of(f);
+  switch (h->precision) {
+    case NSI_FP64:
+      return nodal ? step_p<NSI_FP64, true>(h, fv, o, s) : step_p<NSI_FP64, false>(h, fv, o, s);
+    case NSI_MIXED_F32_ACC64:
+      return nodal ? step_p<NSI_MIXED_F32_ACC64, true>(h, fv, o, s) : step_p<NSI_MIXED_F32_ACC64, false>(h, fv, o, s);
+    default:
+      return nodal ? step_p<NSI_MIXED_F32_ACC32, true>(h, fv, o, s) : step_p<NSI_MIXED_F32_ACC32, false>(h, fv, o, s);
+  }
+}
+
 template <int P>
 static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os, int count,
                             cudaStream_t s) {
@@ -1630,6 +1965,26 @@ nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const
     case NSI_MIXED_F32_ACC64: return batched_p<NSI_MIXED_F32_ACC64>(hs, fs, os, count, s);
     default: return batched_p<NSI_MIXED_F32_ACC32>(hs, fs, os, count, s);
   }
+}
+
+nsi_status nsi_assemble_convective(NsiHandle* h, const NsiFields* f, const void* A_static, void* A_val, void* rhs,
+                                   void* stream) {
+  if (!h || !f || !A_static || !A_val || !rhs) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < 3; ++k)
+    if (!f->u[k]) return fail(NSI_ERR_INVALID_ARG, "velocity component pointer is NULL");
+  if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");
+  const StepView o{A_static, A_val, rhs, nullptr, nullptr, 0.0, 0.0f};
+  return step_dispatch(h, f, o, false, static_cast<cudaStream_t>(stream));
+}
+
+nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void* dt_rho, void* mass_rho, void* stream) {
+  if (!h || !f || !rhs || !dt_rho || !mass_rho) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < 3; ++k)
+    if (!f->u[k]) return fail(NSI_ERR_INVALID_ARG, "velocity component pointer is NULL");
+  if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");
+  const double kmr = f->rho / 24.0;
+  const StepView o{nullptr, nullptr, rhs, dt_rho, mass_rho, kmr, (float)kmr};
+  return step_dispatch(h, f, o, true, static_cast<cudaStream_t>(stream));
 }
 
 nsi_status nsi_assemble_vjp(NsiHandle* h, const NsiFields* f, const void* w, void* grad_u, double* grad_mu,
