@@ -81,11 +81,13 @@ struct GatherPlan {
 //   col   int32 per CSR entry, read only while the records are gathered: it
 //         shares nb1's bytes (nb1 is written after a barrier)
 //   walk  one byte per step (copied as aligned 4-byte words, so S + 8 bytes)
+//   stat  (time-step kernels only) the block's slice of A_static
 // After the element loop, nb0 is reused to stage the finished values in CSR
 // order for the coalesced write-out.
 // Used identically by the host (launch size) and the kernel (carving).
 struct GatherSmem {
   int R, W, L, S, tb, ab, ob, cr;  // ob: bytes of an output value; cr: components staged per write-out round
+  int xs;                          // bytes per CSR entry of the time step's static slice (0: none)
   __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ size_t N() const { return (size_t)R * W; }
   __host__ __device__ size_t nb0() const { return 0; }
@@ -93,7 +95,8 @@ struct GatherSmem {
   __host__ __device__ size_t acc() const { return up16(nb1() + (size_t)2 * tb * N()); }
   __host__ __device__ size_t col() const { return nb1(); }  // (L <= N: 4 L bytes fit in nb1)
   __host__ __device__ size_t walk() const { return up16(acc() + (size_t)ab * N()); }
-  __host__ __device__ size_t total() const { return up16(walk() + (size_t)S + 8); }
+  __host__ __device__ size_t stat() const { return up16(walk() + (size_t)S + 8); }
+  __host__ __device__ size_t total() const { return up16(stat() + (size_t)xs * L); }
   // the write-out stages cr components of the block's L entries in nb0
   __host__ __device__ size_t stage_bytes() const { return (size_t)cr * L * ob; }
   __host__ __device__ bool stage_fits() const { return stage_bytes() <= nb1() - nb0(); }
@@ -110,8 +113,10 @@ __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, i
   g.tb = precision == NSI_FP64 ? 8 : 4;
   g.ab = precision == NSI_MIXED_F32_ACC32 ? 16 : 32;
   if (step) g.ab = precision == NSI_FP64 ? 32 : 16;
+  g.xs = 0;
   g.ob = precision == NSI_MIXED_F32_ACC32 ? 4 : 8;
   g.cr = precision == NSI_MIXED_F32_ACC64 ? 2 : 4;
+  if (step) g.xs = g.ob;  // the block's slice of A_static, copied in before the walk
   return g;
 }
 

@@ -1086,6 +1086,15 @@ __device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f,
   const T2<T>* __restrict__ nb1 = reinterpret_cast<const T2<T>*>(smem + lay.nb1());
   const T kc = kc_of<T>(f);
   const T kmass = kmass_of<T>(f);
+  Out* stat = reinterpret_cast<Out*>(smem + lay.stat());
+  if constexpr (!NODAL) {
+    // the block's slice of A_static, in flight during the walk
+    const Out* As = static_cast<const Out*>(o.A_static) + b.base;
+    for (int k = t; k < b.L; k += R) {
+      if constexpr (sizeof(Out) == 8) cp_async8(stat + k, As + k);
+      else cp_async4(stat + k, As + k);
+    }
+  }
   Acc<P> detsum;
   detsum.zero();
   if (t < b.nrows) {
@@ -1125,22 +1134,22 @@ __device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f,
     __syncthreads();
     // the block's contiguous slice of A: staged in CSR order, then
     // A = A_static + C streamed out coalesced
-    const Out* As = static_cast<const Out*>(o.A_static) + b.base;
     Out* A = static_cast<Out*>(o.A) + b.base;
+    cp_async_wait_all();
     if constexpr (P == NSI_MIXED_F32_ACC64) {
       float2* stage = reinterpret_cast<float2*>(smem + lay.nb0());
       if (t < b.nrows)
         for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
       __syncthreads();
 #pragma unroll 2
-      for (int k = t; k < b.L; k += R) A[k] = As[k] + pair_double(stage[k].x, stage[k].y);
+      for (int k = t; k < b.L; k += R) A[k] = stat[k] + pair_double(stage[k].x, stage[k].y);
     } else {
       Out* stage = reinterpret_cast<Out*>(smem + lay.nb0());
       if (t < b.nrows)
         for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
       __syncthreads();
 #pragma unroll 2
-      for (int k = t; k < b.L; k += R) A[k] = As[k] + stage[k];
+      for (int k = t; k < b.L; k += R) A[k] = stat[k] + stage[k];
     }
   }
 }
