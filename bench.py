@@ -319,7 +319,7 @@ def run_gpu(args, world, rank, local):
         mode = {0: "auto", 1: "color", 2: "atomic", 3: "gather"}[asm.scatter]
         rec = {"ms": mean_ms, "ms_min": min(ms), "ms_median": statistics.median(ms), "steps": steps,
                "kernel_ms": statistics.mean(kms), "elements_per_s": E / (mean_ms * 1e-3), "clocks": clocks,
-               "nnz": asm.nnz, "mode": mode,
+               "nnz": asm.nnz, "mode": mode, "persistent": bool(asm.info().persistent),
                "launches_per_step": {"gather": 2, "atomic": 1, "color": asm.n_colors}[mode]}
         if not args.quick or prec == main_prec:
             rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(7).integers(0, n, 48)]))
@@ -352,7 +352,8 @@ def run_gpu(args, world, rank, local):
     main = results[main_prec]
     ms_max = allreduce_max(main["ms"], world)
     value = world * E / (ms_max * 1e-3)
-    kernel = {"gather": "fan_kernel" if args.fan else "gather_kernel", "atomic": "elem_kernel",
+    gather_name = "fan_kernel" if args.fan else ("gather_persistent_kernel" if main["persistent"] else "gather_kernel")
+    kernel = {"gather": gather_name, "atomic": "elem_kernel",
               "color": "elem_kernel"}[main["mode"]]
     bytes_alg = algorithmic_bytes(E, n, main["nnz"], main_prec)
     peak, peak_src = hbm_peak()

@@ -160,6 +160,10 @@ typedef struct {
     int32_t rows_per_block; /* row-gather launch shape in use: rows per block of the per-row
                                star kernel, -1 for the edge-fan kernel, 0 if unavailable */
     int32_t n_plans;        /* row-gather launch shapes available */
+    int32_t persistent;     /* 1: the row gather runs as a persistent grid (a CTA's next block of
+                               rows copies its column indices and walk while the current one
+                               writes out), 0: one CTA per block of rows */
+    int32_t reserved;
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 

@@ -595,6 +595,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     h->plan.max_block_entries = chosen_L;
     h->plan.max_block_steps = chosen_S;
     h->plan.n_blocks = chosen ? (n + chosen - 1) / chosen : 0;
+    // the persistent grid (next block's phase 0 under the current block's
+    // write-out) measured faster for mixed64 only: 0.505 against 0.545 ms at
+    // the 100^3 cube; mixed32 unchanged, FP64 slower (4.23 against 3.29 ms)
+    h->persistent = h->precision == NSI_MIXED_F32_ACC64;
   }
 
   // 8. upload
@@ -728,6 +732,8 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->device_bytes = h->device_bytes;
   info->rows_per_block = h->use_fan ? -1 : h->plan.rows_per_block;
   info->n_plans = h->n_plans;
+  info->persistent = h->persistent && !h->use_fan ? 1 : 0;
+  info->reserved = 0;
   return NSI_OK;
 }
 

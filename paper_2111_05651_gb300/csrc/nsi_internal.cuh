@@ -153,6 +153,7 @@ struct NsiHandle {
   int32_t* fan_blk = nullptr;   // [fan_blocks + 1] first row of every fan block
   int64_t fan_blocks = 0;
   bool use_fan = false;         // row-gather mode runs the edge-fan kernel
+  bool persistent = false;      // row-gather mode runs the persistent grid (set by create: mixed64)
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
   int n_plans = 0;

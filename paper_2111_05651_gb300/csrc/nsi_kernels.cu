@@ -649,63 +649,88 @@ struct BlockRows {
   V3<T> uni;
 };
 
-// Phases 0 and 1 of a row-gather block, shared by the full assembly and the
-// time-step kernels: the row's scalars; the block's column indices and walk
-// steps (asynchronous copies); every neighbour's record (calculate_transients
-// for the row, asynchronous copies all in flight at once), turned into edge
-// vectors d = x_j - x_i (the row's own record, its diagonal slot, gives the
-// origin) and velocities in nb0/nb1; the accumulators zeroed.  Returns false
-// (block-uniform) if the block does not fit the layout.
-template <int P, bool DEBUG, typename Accum>
-__device__ __forceinline__ bool stage_block(const MeshView& m, const FieldView& f, int64_t r0, unsigned char* smem,
-                                            const GatherSmem& lay, Accum& acc, BlockRows<typename Prec<P>::T>& b) {
+// Phase 0 of a block: its bounds and the row's scalars (plain loads, in
+// flight until first used), then the asynchronous copies of the block's
+// column indices (into nb1) and walk steps.
+template <typename T>
+struct Phase0 {
+  int64_t r0;
+  int nrows, L, S;
+  int32_t base, sbase, rs, re, s0, s1;
+  int dp;
+  V3<T> uni;
+};
+
+template <int P>
+__device__ __forceinline__ Phase0<typename Prec<P>::T> load_phase0(const MeshView& m, const FieldView& f, int64_t r0) {
   using T = typename Prec<P>::T;
+  Phase0<T> p;
   const int R = blockDim.x;
   const int t = threadIdx.x;
   const int64_t r_end = min(r0 + (int64_t)R, m.n);
-  const int nrows = (int)(r_end - r0);
-  const int32_t base = m.row_ptr[r0], bend = m.row_ptr[r_end];
-  const int L = bend - base;
-  const int32_t sbase = m.walk_ptr[r0], send = m.walk_ptr[r_end];
-  const int S = send - sbase;
-  if (DEBUG && (L > lay.L || S > lay.S || R != lay.R)) {
+  p.r0 = r0;
+  p.nrows = (int)(r_end - r0);
+  p.base = m.row_ptr[r0];
+  p.L = m.row_ptr[r_end] - p.base;
+  p.sbase = m.walk_ptr[r0];
+  p.S = m.walk_ptr[r_end] - p.sbase;
+  p.rs = p.re = p.s0 = p.s1 = 0;
+  p.dp = 0;
+  p.uni = V3<T>{T(0), T(0), T(0)};
+  const int soff = p.sbase & 3;  // walk bytes are copied as aligned 4-byte words
+  if (t < p.nrows) {
+    const int64_t i = r0 + t;
+    p.rs = m.row_ptr[i];
+    p.re = m.row_ptr[i + 1];
+    p.s0 = m.walk_ptr[i] - p.sbase + soff;
+    p.s1 = m.walk_ptr[i + 1] - p.sbase + soff;
+    p.dp = m.diag_pos[i];
+    p.uni = load_vec<T>(f.un, i);
+  }
+  return p;
+}
+
+template <bool DEBUG, typename T>
+__device__ __forceinline__ void issue_phase0(const MeshView& m, unsigned char* smem, const GatherSmem& lay,
+                                             const Phase0<T>& p) {
+  const int R = blockDim.x;
+  const int t = threadIdx.x;
+  if (DEBUG && (p.L > lay.L || p.S > lay.S || R != lay.R)) return;  // reported by stage_records
+  int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
+  uint8_t* walk = smem + lay.walk();
+  for (int k = t; k < p.L; k += R) cp_async4(&col[k], m.col_idx + p.base + k);
+  const int soff = p.sbase & 3;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(m.walk + (p.sbase - soff));
+  const int words = (p.S + soff + 3) >> 2;
+  for (int k = t; k < words; k += R) cp_async4(reinterpret_cast<uint32_t*>(walk) + k, src + k);
+}
+
+// Phase 1 of a block whose phase-0 copies are in flight: every neighbour's
+// record (calculate_transients for the row, asynchronous copies all in
+// flight at once), turned into edge vectors d = x_j - x_i (the row's own
+// record, its diagonal slot, gives the origin) and velocities in nb0/nb1; the
+// accumulators zeroed.  Returns false (block-uniform) if the block does not
+// fit the layout.
+template <int P, bool DEBUG, typename Accum>
+__device__ __forceinline__ bool stage_records(const MeshView& m, unsigned char* smem, const GatherSmem& lay,
+                                              Accum& acc, const Phase0<typename Prec<P>::T>& p,
+                                              BlockRows<typename Prec<P>::T>& b) {
+  using T = typename Prec<P>::T;
+  const int R = blockDim.x;
+  const int t = threadIdx.x;
+  if (DEBUG && (p.L > lay.L || p.S > lay.S || R != lay.R)) {
     if (t == 0) atomicOr(m.err, ERR_STAR);
     return false;
   }
   T4<T>* __restrict__ nb0 = reinterpret_cast<T4<T>*>(smem + lay.nb0());
   T2<T>* __restrict__ nb1 = reinterpret_cast<T2<T>*>(smem + lay.nb1());
-  int32_t* col = reinterpret_cast<int32_t*>(smem + lay.col());
-  uint8_t* walk = smem + lay.walk();
-
-  // phase 0: the row's scalars; the block's column indices and walk steps by
-  // asynchronous copies (all in flight)
-  const int64_t i = r0 + t;
-  int32_t rs = 0, re = 0, s0 = 0, s1 = 0;
-  int dp = 0;
-  V3<T> uni{T(0), T(0), T(0)};
-  const int soff = sbase & 3;  // walk bytes are copied as aligned 4-byte words
-  if (t < nrows) {
-    rs = m.row_ptr[i];
-    re = m.row_ptr[i + 1];
-    s0 = m.walk_ptr[i] - sbase + soff;
-    s1 = m.walk_ptr[i + 1] - sbase + soff;
-    dp = m.diag_pos[i];
-    uni = load_vec<T>(f.un, i);
-  }
-  for (int k = t; k < L; k += R) cp_async4(&col[k], m.col_idx + base + k);
-  {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(m.walk + (sbase - soff));
-    const int words = (S + soff + 3) >> 2;
-    for (int k = t; k < words; k += R) cp_async4(reinterpret_cast<uint32_t*>(walk) + k, src + k);
-  }
+  const int32_t* col = reinterpret_cast<const int32_t*>(smem + lay.col());
   cp_async_wait_all();
   __syncthreads();
 
-  const int len = re - rs;
-  const int lb = rs - base;
-  if (t < nrows) {
-    // phase 1 (calculate_transients for the row): every neighbour's record,
-    // by asynchronous copies all in flight at once
+  const int len = p.re - p.rs;
+  const int lb = p.rs - p.base;
+  if (t < p.nrows) {
     const unsigned char* recs = static_cast<const unsigned char*>(m.rec);
     constexpr int RB = P == NSI_FP64 ? 64 : 32;
     for (int q = 0, k = t; q < len; ++q, k += R) {
@@ -729,12 +754,10 @@ __device__ __forceinline__ bool stage_block(const MeshView& m, const FieldView& 
   // every row's column indices have been read: nb1, which holds them, may now
   // be written
   __syncthreads();
-  if (t < nrows) {
+  if (t < p.nrows) {
     cp_async_wait_all();
-    // edge vectors d = x_j - x_i; the row's own record (its diagonal slot)
-    // gives the origin.  The slots are this thread's own.
     if (len > 0) {
-      const int kd = dp * R + t;
+      const int kd = p.dp * R + t;
       if constexpr (P == NSI_FP64) {
         const T4<T> hi = nb0[kd];
         const V3<T> xi{hi.x, hi.y, hi.z};
@@ -762,22 +785,30 @@ __device__ __forceinline__ bool stage_block(const MeshView& m, const FieldView& 
       }
     }
   }
-  b = BlockRows<T>{R, t, nrows, L, len, lb, s0, s1, dp, i, base, uni};
+  b = BlockRows<T>{R, t, p.nrows, p.L, len, lb, p.s0, p.s1, p.dp, p.r0 + t, p.base, p.uni};
   return true;
 }
 
-// one block of rows [r0, r0 + blockDim.x) of one mesh
+// Phases 0 and 1 of a row-gather block, shared by the full assembly and the
+// time-step kernels.
+template <int P, bool DEBUG, typename Accum>
+__device__ __forceinline__ bool stage_block(const MeshView& m, const FieldView& f, int64_t r0, unsigned char* smem,
+                                            const GatherSmem& lay, Accum& acc, BlockRows<typename Prec<P>::T>& b) {
+  const Phase0<typename Prec<P>::T> p = load_phase0<P>(m, f, r0);
+  issue_phase0<DEBUG>(m, smem, lay, p);
+  return stage_records<P, DEBUG>(m, smem, lay, acc, p, b);
+}
+
+// phase 2 of a staged block: every element of each row's star, the diagonal
+// and the RHS; ends with a barrier (nb1 and the walk bytes are free after it)
 template <int P, bool DEBUG>
-__device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& f, const OutView& o, int64_t r0,
-                                            unsigned char* smem, const GatherSmem& lay) {
+__device__ __forceinline__ void gather_compute(const MeshView& m, const FieldView& f, const OutView& o,
+                                               unsigned char* smem, const GatherSmem& lay, AccSmem<P>& acc,
+                                               const BlockRows<typename Prec<P>::T>& b) {
   using T = typename Prec<P>::T;
   using Out = typename Prec<P>::Out;
-  AccSmem<P> acc(smem + lay.acc(), lay.N());
-  BlockRows<T> b;
-  if (!stage_block<P, DEBUG>(m, f, r0, smem, lay, acc, b)) return;
-  const int R = b.R, t = b.t, nrows = b.nrows, L = b.L, len = b.len, lb = b.lb, s0 = b.s0, s1 = b.s1, dp = b.dp;
+  const int R = b.R, t = b.t, nrows = b.nrows, len = b.len, s0 = b.s0, s1 = b.s1, dp = b.dp;
   const int64_t i = b.i;
-  const int32_t base = b.base;
   const V3<T> uni = b.uni;
   const T4<T>* __restrict__ nb0 = reinterpret_cast<const T4<T>*>(smem + lay.nb0());
   const T2<T>* __restrict__ nb1 = reinterpret_cast<const T2<T>*>(smem + lay.nb1());
@@ -843,6 +874,18 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
     }
   }
   __syncthreads();
+}
+
+// phase 3 of a block: its contiguous slice of A and G (uses nb0 and acc only)
+template <int P>
+__device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView& o, unsigned char* smem,
+                                                const GatherSmem& lay, AccSmem<P>& acc,
+                                                const BlockRows<typename Prec<P>::T>& b) {
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  const int R = b.R, t = b.t, nrows = b.nrows, L = b.L, len = b.len, lb = b.lb;
+  const int32_t base = b.base;
+  const T kg = (T)(-1.0 / 24.0);
   // phase 3: the block's contiguous slice of A and G.  Every thread moves its
   // own row's finished values into CSR order (nb0 reused as staging), then the
   // block streams the slice out coalesced.
@@ -896,6 +939,17 @@ __device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& 
       if (half == 0) __syncthreads();
     }
   }
+}
+
+// one block of rows [r0, r0 + blockDim.x) of one mesh
+template <int P, bool DEBUG>
+__device__ __forceinline__ void gather_rows(const MeshView& m, const FieldView& f, const OutView& o, int64_t r0,
+                                            unsigned char* smem, const GatherSmem& lay) {
+  AccSmem<P> acc(smem + lay.acc(), lay.N());
+  BlockRows<typename Prec<P>::T> b;
+  if (!stage_block<P, DEBUG>(m, f, r0, smem, lay, acc, b)) return;
+  gather_compute<P, DEBUG>(m, f, o, smem, lay, acc, b);
+  gather_writeout<P>(m, o, smem, lay, acc, b);
 }
 
 // ------------------------------------------- cached-geometry time step ---
@@ -1433,6 +1487,37 @@ __global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, Ou
   gather_rows<P, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, smem_raw, lay);
 }
 
+// The row gather as a persistent grid (one CTA per resident block slot): a
+// CTA's next block of rows loads its bounds and row scalars while the current
+// block walks, and copies its column indices and walk steps (into nb1 and the
+// walk region, free after the walk) while the current block writes out.
+template <int P, bool DEBUG>
+__global__ void __launch_bounds__(128) gather_persistent_kernel(MeshView m, FieldView f, OutView o, GatherSmem lay,
+                                                                int64_t nblocks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using T = typename Prec<P>::T;
+  int64_t blk = blockIdx.x;
+  if (blk >= nblocks) return;
+  const int R = blockDim.x;
+  AccSmem<P> acc(smem_raw + lay.acc(), lay.N());
+  Phase0<T> p = load_phase0<P>(m, f, blk * R);
+  issue_phase0<DEBUG>(m, smem_raw, lay, p);
+  while (true) {
+    BlockRows<T> b;
+    if (!stage_records<P, DEBUG>(m, smem_raw, lay, acc, p, b)) return;
+    const int64_t nxt = blk + gridDim.x;
+    const bool more = nxt < nblocks;  // block-uniform
+    Phase0<T> pn = p;
+    if (more) pn = load_phase0<P>(m, f, nxt * R);
+    gather_compute<P, DEBUG>(m, f, o, smem_raw, lay, acc, b);
+    if (more) issue_phase0<DEBUG>(m, smem_raw, lay, pn);
+    gather_writeout<P>(m, o, smem_raw, lay, acc, b);
+    if (!more) return;
+    blk = nxt;
+    p = pn;
+  }
+}
+
 // ------------------------------------------------------ batched kernel ---
 struct BatchItem {
   MeshView m;
@@ -1643,6 +1728,9 @@ static nsi_status set_gather_smem() {
   std::call_once(once, [] {
     err = cudaFuncSetAttribute(gather_kernel<P, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(gather_persistent_kernel<P, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+    if (err == cudaSuccess)
       err = cudaFuncSetAttribute(batched_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute(gather smem)");
@@ -1696,6 +1784,21 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
   const size_t smem = lay.total();
+  if (h->persistent) {
+    int per_sm = 0, sms = 0, dev = 0;
+    NSI_CUDA(cudaGetDevice(&dev));
+    NSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (h->debug)
+      NSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_persistent_kernel<P, true>, R, smem));
+    else
+      NSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_persistent_kernel<P, false>, R, smem));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(h->plan.n_blocks, (int64_t)std::max(1, per_sm) * sms));
+    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
+    if (h->debug) gather_persistent_kernel<P, true><<<grid, R, smem, s>>>(m, f, o, lay, h->plan.n_blocks);
+    else gather_persistent_kernel<P, false><<<grid, R, smem, s>>>(m, f, o, lay, h->plan.n_blocks);
+    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
+    return check_launch("gather_persistent_kernel");
+  }
   if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
   if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
   else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);

@@ -46,7 +46,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(nsi.NsiOptions) == 32
     assert ctypes.sizeof(nsi.NsiFields) == 72
     assert ctypes.sizeof(nsi.NsiOutputs) == 24
-    assert ctypes.sizeof(nsi.NsiInfo) == 56
+    assert ctypes.sizeof(nsi.NsiInfo) == 64
 
 
 def test_null_arguments_rejected_without_gpu():
