@@ -74,6 +74,9 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->err);
   cudaFree(h->rec);
   cudaFree(h->stage);
+  for (cudaEvent_t e : h->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
 }
 
@@ -604,6 +607,7 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   // 8. upload
   nsi_status st;
   if ((st = dev_upload(h, &h->row_ptr, row_ptr.data(), n + 1, s))) return st;
+  h->row_ptr_host = row_ptr;
   if ((st = dev_upload(h, &h->col_idx, col.data(), nnz, s))) return st;
   if ((st = dev_upload(h, &h->lnods, reinterpret_cast<const int4*>(ln.data()), E, s))) return st;
   if ((st = dev_upload(h, &h->color_elems, color_elems.data(), E, s))) return st;

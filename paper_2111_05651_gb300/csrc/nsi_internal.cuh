@@ -173,6 +173,12 @@ struct NsiHandle {
   // staging for nsi_assemble_host (allocated on first use)
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // host-buffer calls: the CSR row starts on the host, and a stream and
+  // events on which finished chunks of the outputs go to the host while the
+  // next chunk is assembled
+  std::vector<int32_t> row_ptr_host;  // [n+1]
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t chunk_ev[8] = {};
 };
 
 namespace nsi {

@@ -1482,9 +1482,10 @@ __global__ void __launch_bounds__(FAN_BLOCK) fan_kernel(MeshView m, FieldView f,
 }
 
 template <int P, bool DEBUG>
-__global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, OutView o, GatherSmem lay) {
+__global__ void __launch_bounds__(128) gather_kernel(MeshView m, FieldView f, OutView o, GatherSmem lay,
+                                                     int64_t block0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  gather_rows<P, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, smem_raw, lay);
+  gather_rows<P, DEBUG>(m, f, o, (block0 + blockIdx.x) * blockDim.x, smem_raw, lay);
 }
 
 // The row gather as a persistent grid (one CTA per resident block slot): a
@@ -1800,8 +1801,8 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
     return check_launch("gather_persistent_kernel");
   }
   if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
-  if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
-  else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
+  if (h->debug) gather_kernel<P, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay, 0);
+  else gather_kernel<P, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay, 0);
   if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
   return check_launch("gather_kernel");
 }
@@ -2041,13 +2042,65 @@ static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const Out
   }
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
-  gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay);
+  gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay, 0);
   return check_launch("gather_kernel (no-alloc)");
 }
 
 }  // namespace nsi
 
 using namespace nsi;
+
+// Host-buffer call in the row-gather mode: the blocks of rows are assembled
+// in chunks, and each finished chunk's slices of A, G and rhs go to the host
+// on the handle's copy stream while the next chunk is assembled (the copies
+// are the larger part of such a call).
+template <int P>
+static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOutputs* od, const NsiOutputs* o,
+                                 cudaStream_t s) {
+  using Out = typename Prec<P>::Out;
+  constexpr int C = (int)(sizeof(h->chunk_ev) / sizeof(h->chunk_ev[0]));
+  if (!h->copy_stream) NSI_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : h->chunk_ev)
+    if (!e) NSI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
+  if (st) return st;
+  const MeshView m = view_of(h);
+  const FieldView fv = fields_of(fd);
+  const OutView ov{od->A_val, od->G_val, od->rhs};
+  const int R = h->plan.rows_per_block;
+  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
+  const size_t smem = lay.total();
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, fv, h->rec);
+  const int64_t nb = h->plan.n_blocks;
+  const int chunks = (int)std::min<int64_t>(C, nb);
+  const Out* dA = static_cast<const Out*>(od->A_val);
+  const Out* dG = static_cast<const Out*>(od->G_val);
+  const Out* dR = static_cast<const Out*>(od->rhs);
+  Out* hA = static_cast<Out*>(o->A_val);
+  Out* hG = static_cast<Out*>(o->G_val);
+  Out* hR = static_cast<Out*>(o->rhs);
+  for (int c = 0; c < chunks; ++c) {
+    const int64_t b0 = nb * c / chunks, b1 = nb * (c + 1) / chunks;
+    if (h->debug) gather_kernel<P, true><<<b1 - b0, R, smem, s>>>(m, fv, ov, lay, b0);
+    else gather_kernel<P, false><<<b1 - b0, R, smem, s>>>(m, fv, ov, lay, b0);
+    st = check_launch("gather_kernel (host chunk)");
+    if (st) return st;
+    NSI_CUDA(cudaEventRecord(h->chunk_ev[c], s));
+    NSI_CUDA(cudaStreamWaitEvent(h->copy_stream, h->chunk_ev[c], 0));
+    const int64_t r0 = b0 * R, r1 = std::min<int64_t>(h->n, b1 * R);
+    const int64_t e0 = h->row_ptr_host[r0], e1 = h->row_ptr_host[r1];
+    const size_t eb = sizeof(Out) * (size_t)(e1 - e0), rb = sizeof(Out) * (size_t)(r1 - r0);
+    // A's slice, then the three components of G and of rhs (equal slices at a
+    // fixed pitch) as one 2D copy each
+    NSI_CUDA(cudaMemcpyAsync(hA + e0, dA + e0, eb, cudaMemcpyDeviceToHost, h->copy_stream));
+    const size_t gp = sizeof(Out) * (size_t)h->nnz, rp = sizeof(Out) * (size_t)h->n;
+    NSI_CUDA(cudaMemcpy2DAsync(hG + e0, gp, dG + e0, gp, eb, 3, cudaMemcpyDeviceToHost, h->copy_stream));
+    NSI_CUDA(cudaMemcpy2DAsync(hR + r0, rp, dR + r0, rp, rb, 3, cudaMemcpyDeviceToHost, h->copy_stream));
+  }
+  NSI_CUDA(cudaStreamSynchronize(h->copy_stream));
+  NSI_CUDA(cudaStreamSynchronize(s));
+  return NSI_OK;
+}
 
 extern "C" {
 
@@ -2247,6 +2300,16 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f, const NsiOutputs*
   }
   char* ob = base + ((u_bytes + 255) / 256) * 256;
   NsiOutputs od{ob, ob + osz * h->nnz, ob + osz * 4 * h->nnz};
+  if (resolve_mode(h, NSI_SCATTER_AUTO) == NSI_SCATTER_GATHER && !h->use_fan && h->n > 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");
+    switch (h->precision) {
+      case NSI_FP64: return host_chunked_p<NSI_FP64>(h, &fd, &od, o, s);
+      case NSI_MIXED_F32_ACC64: return host_chunked_p<NSI_MIXED_F32_ACC64>(h, &fd, &od, o, s);
+      default: return host_chunked_p<NSI_MIXED_F32_ACC32>(h, &fd, &od, o, s);
+    }
+  }
   st = assemble_dispatch(h, &fd, &od, NSI_SCATTER_AUTO, s);
   if (st) return st;
   NSI_CUDA(cudaMemcpyAsync(o->A_val, od.A_val, osz * h->nnz, cudaMemcpyDeviceToHost, s));
