@@ -12,6 +12,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,3 +76,19 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["unit"] == "elements/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_batch_meshes_sharded_over_ranks():
+    """The batched workload splits its independent meshes over the ranks:
+    each mesh on exactly one rank, element counts balanced within the largest
+    mesh (longest-first greedy), one rank = the whole batch."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sizes = [6 * int(n) ** 3 for n in np.random.default_rng(3).integers(10, 61, size=64)]
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.shard_meshes(sizes, world)
+        assert sorted(i for p in parts for i in p) == list(range(64))
+        loads = [sum(sizes[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+    assert bench.shard_meshes(sizes, 1) == [list(range(64))]
