@@ -1532,20 +1532,53 @@ struct BatchArgs {
   BatchItem item[NSI_MAX_BATCH];
 };
 
+// the item (mesh) of global block b: the last item with block0 <= b
+__device__ __forceinline__ const BatchItem& batch_item(const BatchArgs& args, int64_t b) {
+  int lo = 0, hi = args.count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (args.item[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return args.item[lo];
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ BatchArgs args, GatherSmem lay) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int64_t b = blockIdx.x; b < args.total_blocks; b += gridDim.x) {
-    // mesh of global block b: last item with block0 <= b
-    int lo = 0, hi = args.count - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (args.item[mid].block0 <= b) lo = mid;
-      else hi = mid - 1;
+  if constexpr (P == NSI_MIXED_F32_ACC64) {
+    // as gather_persistent_kernel: the next block's phase 0 runs under the
+    // current block's write-out (the next block may belong to another mesh)
+    using T = typename Prec<P>::T;
+    int64_t b = blockIdx.x;
+    if (b >= args.total_blocks) return;
+    const int R = blockDim.x;
+    AccSmem<P> acc(smem_raw + lay.acc(), lay.N());
+    const BatchItem* it = &batch_item(args, b);
+    Phase0<T> p = load_phase0<P>(it->m, it->f, (b - it->block0) * R);
+    issue_phase0<false>(it->m, smem_raw, lay, p);
+    while (true) {
+      BlockRows<T> rows;
+      stage_records<P, false>(it->m, smem_raw, lay, acc, p, rows);
+      const int64_t nxt = b + gridDim.x;
+      const bool more = nxt < args.total_blocks;  // block-uniform
+      const BatchItem* itn = more ? &batch_item(args, nxt) : it;
+      Phase0<T> pn = p;
+      if (more) pn = load_phase0<P>(itn->m, itn->f, (nxt - itn->block0) * R);
+      gather_compute<P, false>(it->m, it->f, it->o, smem_raw, lay, acc, rows);
+      if (more) issue_phase0<false>(itn->m, smem_raw, lay, pn);
+      gather_writeout<P>(it->m, it->o, smem_raw, lay, acc, rows);
+      if (!more) return;
+      b = nxt;
+      it = itn;
+      p = pn;
     }
-    const BatchItem& it = args.item[lo];
-    gather_rows<P, false>(it.m, it.f, it.o, (b - it.block0) * blockDim.x, smem_raw, lay);
-    __syncthreads();  // the next block reuses the shared records
+  } else {
+    for (int64_t b = blockIdx.x; b < args.total_blocks; b += gridDim.x) {
+      const BatchItem& it = batch_item(args, b);
+      gather_rows<P, false>(it.m, it.f, it.o, (b - it.block0) * blockDim.x, smem_raw, lay);
+      __syncthreads();  // the next block reuses the shared records
+    }
   }
 }
 
