@@ -27,12 +27,14 @@ nsi_status cuda_fail(cudaError_t e, const char* what);
 // device error word bits (set by kernels built with debug checks)
 enum : unsigned { ERR_BAD_INDEX = 1u, ERR_NOT_IN_PATTERN = 2u, ERR_STAR = 4u };
 
-// Row-gather ("pull") map: for CSR row i, one 16-bit word per element that
-// contains node i, in increasing element order: the positions, inside row i's
-// column list, of the element's other three nodes (5 bits each), ordered so
-// that (i, j1, j2, j3) is an even permutation of the element's node order
-// (hence a positively oriented tet).  Rows longer than 32 entries cannot be
-// encoded; such meshes do not support the gather mode.
+// Row-gather ("pull") map, built at create time: for CSR row i, one 16-bit
+// word per element that contains node i (the row's star): the positions,
+// inside row i's column list, of the element's other three nodes (5 bits
+// each), ordered so that (i, j1, j2, j3) is an even permutation of the
+// element's node order (hence a positively oriented tet).  The kernels read
+// the element walk encoded from these words (WALK_* below) and the edge-fan
+// map.  Rows longer than 32 entries cannot be encoded; such meshes do not
+// support the gather mode.
 constexpr int STAR_BITS = 5;
 constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
 // One step of a row's element walk (one byte): the row position of the node

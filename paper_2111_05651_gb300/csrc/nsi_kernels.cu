@@ -4,12 +4,21 @@
 //                   perform_assembly_in_global_system of Listing 1 fused),
 //                   scatter by global atomics or, colour by colour, by plain
 //                   read-add-write (deterministic)
-//   gather_kernel   one CSR row per thread: the row's owner visits every
-//                   element around its node, accumulates the row privately
-//                   and the block writes its contiguous slice of A, G and rhs
-//                   once, coalesced (no atomics, no zeroing, deterministic)
-//   batched_kernel  gather_kernel over many meshes in one persistent launch
+//   gather_kernel   one CSR row per thread: the row's owner walks every
+//                   element around its node (the element walk built at
+//                   create), accumulates the row privately and the block
+//                   writes its contiguous slice of A, G and rhs once,
+//                   coalesced (no atomics, no zeroing, deterministic)
+//   gather_persistent_kernel  the same as a persistent grid (a CTA's next
+//                   block of rows starts its copies under the current
+//                   block's write-out)
+//   fan_kernel      one CSR entry per thread, walking the ring of elements
+//                   around its edge (autotuning candidate)
+//   batched_kernel  the row gather over many meshes in one persistent launch
+//   step_kernel     one time step with cached geometry (A_static + C(u),
+//                   rhs), or the paper's per-node outputs
 //   vjp_kernel      adjoint of R(u, mu) = A(u) u - b, element per thread
+//   residual_kernel R(u, mu) without the matrix
 //
 // Formulas: see the element-arithmetic comment in nsi_internal.cuh.
 #include <algorithm>
