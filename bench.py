@@ -362,9 +362,10 @@ def run_gpu(args, world, rank, local):
         "metric": "tet elements assembled/s", "value": value, "unit": "elements/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed64": "f32 (f64 output)", "mixed32": "f32"}[main_prec],
+        "dtype": {"fp64": "f64", "mixed64": "f32", "mixed32": "f32"}[main_prec],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": main_prec, "scatter": main["mode"],
+                   "output_dtype": {"fp64": "f64", "mixed64": "f64", "mixed32": "f32"}[main_prec],
                    "elements": E, "nodes": n, "nnz": main["nnz"],
                    "l2": "flushed (256 MiB write) before every timed step; working set > L2",
                    "replicas": "each rank assembles its own copy of the workload" if world > 1 else None},
@@ -461,7 +462,7 @@ def run_batch(args, world, rank, local):
         print(json.dumps({
             "metric": "tet elements assembled/s", "value": E / (ms * 1e-3), "unit": "elements/s",
             "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch64"], "meshes": len(all_meshes), "elements": E,
                        "meshes_on_rank0": len(meshes),
                        "precision": prec, "launches_per_step": "1 batched + 64 pack + velocity update",
@@ -568,7 +569,7 @@ def run_step(args, world, rank, local):
         print(json.dumps({"metric": "tet elements stepped/s (cached-geometry convective step)",
                           "value": world * E / (ms * 1e-3), "unit": "elements/s", "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                          "scaling": "weak", "dtype": "f32 (f64 output)", "data": "synthetic",
+                          "scaling": "weak", "dtype": "f32", "data": "synthetic",
                           "config": {"workload": WORKLOADS["step100"], "precision": "mixed64",
                                      "l2": "flushed (256 MiB write) before every timed step"},
                           "roofline": {"bound": "hbm", "achieved": m["achieved_gbs"], "peak": peak, "unit": "GB/s",
