@@ -163,7 +163,11 @@ typedef struct {
     int32_t persistent;     /* 1: the row gather runs as a persistent grid (a CTA's next block of
                                rows copies its column indices and walk while the current one
                                writes out), 0: one CTA per block of rows */
-    int32_t reserved;
+    int32_t exact_rows;     /* mixed modes: rows of the nodes of badly shaped elements
+                               (|d1||d2||d3| > 16 |det| from any node); after every assembly or
+                               time step these rows are recomputed in double from the coordinates
+                               and overwritten (a float determinant of such an element carries
+                               about that ratio times the float rounding of its edge vectors) */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 

@@ -66,6 +66,9 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->walk_ptr);
   cudaFree(h->walk);
   cudaFree(h->diag_pos);
+  cudaFree(h->exact_list);
+  cudaFree(h->exact_ptr);
+  cudaFree(h->exact_inc);
   cudaFree(h->fan);
   cudaFree(h->fan_blk);
   cudaFree(h->xyz64);
@@ -604,6 +607,43 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     h->persistent = h->precision == NSI_MIXED_F32_ACC64;
   }
 
+  // 7b. badly shaped elements (mixed modes): a float determinant of an
+  // element with |d1||d2||d3| > EXACT_RATIO |det| (edge vectors from any of its
+  // nodes) would carry about that ratio times the float rounding of the edge
+  // vectors.  The rows of all four nodes of such an element are listed; after
+  // the assembly they are recomputed in double (exact_rows_kernel).
+  std::vector<int32_t> exact_list, exact_ptr;
+  std::vector<uint32_t> exact_inc;
+  if (h->precision != NSI_FP64) {
+    std::vector<uint8_t> flag(n, 0);
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t* v = &ln[4 * e];
+      double worst = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        const V3<double> x0{X[v[a]], Y[v[a]], Z[v[a]]};
+        V3<double> d[3];
+        for (int b = 0, c = 0; b < 4; ++b)
+          if (b != a) d[c++] = sub(V3<double>{X[v[b]], Y[v[b]], Z[v[b]]}, x0);
+        const double det = std::fabs(dot(d[0], cross(d[1], d[2])));
+        const double had = std::sqrt(dot(d[0], d[0]) * dot(d[1], d[1]) * dot(d[2], d[2]));
+        worst = std::max(worst, had / det);
+      }
+      if (worst > EXACT_RATIO)
+        for (int a = 0; a < 4; ++a) flag[v[a]] = 1;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      if (flag[i] && row_len[i] <= STAR_MAX_ROW) exact_list.push_back((int32_t)i);
+    h->exact_rows = (int64_t)exact_list.size();
+    // every listed row's incident elements (element * 4 + local index of the node)
+    exact_ptr.assign(exact_list.size() + 1, 0);
+    for (size_t r = 0; r < exact_list.size(); ++r) {
+      const int64_t i = exact_list[r];
+      for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) exact_inc.push_back((uint32_t)inc[t]);
+      exact_ptr[r + 1] = (int32_t)exact_inc.size();
+    }
+    if (E > (int64_t)(UINT32_MAX >> 2)) h->exact_rows = 0;  // not encodable: keep the float results
+  }
+
   // 8. upload
   nsi_status st;
   if ((st = dev_upload(h, &h->row_ptr, row_ptr.data(), n + 1, s))) return st;
@@ -622,6 +662,11 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->walk_ptr, walk_ptr.data(), n + 1, s))) return st;
     if ((st = dev_upload(h, &h->walk, walk.data(), walk.size(), s))) return st;
     if ((st = dev_upload(h, &h->diag_pos, diag.data(), n, s))) return st;
+  }
+  if (h->exact_rows > 0) {
+    if ((st = dev_upload(h, &h->exact_list, exact_list.data(), exact_list.size(), s))) return st;
+    if ((st = dev_upload(h, &h->exact_ptr, exact_ptr.data(), exact_ptr.size(), s))) return st;
+    if ((st = dev_upload(h, &h->exact_inc, exact_inc.data(), exact_inc.size(), s))) return st;
   }
   if (h->precision == NSI_FP64) {
     if ((st = dev_upload(h, &h->xyz64, xyz64.data(), n, s))) return st;
@@ -737,7 +782,7 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->rows_per_block = h->use_fan ? -1 : h->plan.rows_per_block;
   info->n_plans = h->n_plans;
   info->persistent = h->persistent && !h->use_fan ? 1 : 0;
-  info->reserved = 0;
+  info->exact_rows = (int32_t)std::min<int64_t>(h->exact_rows, INT32_MAX);
   return NSI_OK;
 }
 

@@ -37,6 +37,10 @@ enum : unsigned { ERR_BAD_INDEX = 1u, ERR_NOT_IN_PATTERN = 2u, ERR_STAR = 4u };
 // support the gather mode.
 constexpr int STAR_BITS = 5;
 constexpr int STAR_MAX_ROW = 1 << STAR_BITS;
+// an element with |d1||d2||d3| > EXACT_RATIO |det| (edge vectors from any of
+// its nodes) is "badly shaped": in the mixed modes the rows of its nodes are
+// recomputed in double after the assembly
+constexpr double EXACT_RATIO = 16.0;
 // One step of a row's element walk (one byte): the row position of the node
 // it brings into the window, whether the element formed by the window and that
 // node is evaluated, the element's orientation in window order, and which
@@ -156,6 +160,10 @@ struct NsiHandle {
   int64_t fan_blocks = 0;
   bool use_fan = false;         // row-gather mode runs the edge-fan kernel
   bool persistent = false;      // row-gather mode runs the persistent grid (set by create: mixed64)
+  int64_t exact_rows = 0;       // mixed modes: rows recomputed in double (badly shaped elements)
+  int32_t* exact_list = nullptr;  // [exact_rows] their node ids
+  int32_t* exact_ptr = nullptr;   // [exact_rows + 1] into exact_inc
+  uint32_t* exact_inc = nullptr;  // element * 4 + local index of the row's node
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
   int n_plans = 0;

@@ -1223,6 +1223,111 @@ __global__ void __launch_bounds__(128) step_kernel(MeshView m, FieldView f, Step
   step_rows<P, NODAL, DEBUG>(m, f, o, (int64_t)blockIdx.x * blockDim.x, smem_raw, lay);
 }
 
+// ------------------------------------------------ badly shaped elements ---
+// Rows listed at create (mixed modes: the rows of the nodes of an element with
+// |d1||d2||d3| > EXACT_RATIO |det|) are recomputed after the assembly with
+// every element of their star evaluated in double from the coordinates
+// (leading + residual float parts) and velocities, and their entries
+// overwritten: a float determinant of such an element would carry about that
+// ratio times the float rounding of its edge vectors.  One thread per row,
+// its sums in a local array.  MODE 0: A, G and rhs; 1: rhs only (the time
+// step: the convection does not involve the determinant); 2: rhs, dt_rho and
+// mass_rho.
+template <int P, int MODE>
+__global__ void __launch_bounds__(64) exact_rows_kernel(MeshView m, FieldView f, void* A, void* G, void* rhs,
+                                                        void* dt_rho, void* mass_rho, double kmr, const int32_t* rows,
+                                                        const int32_t* ptr, const uint32_t* inc, int64_t count) {
+  using Out = typename Prec<P>::Out;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const int64_t i = rows[r];
+  const int32_t rs = m.row_ptr[i], len = m.row_ptr[i + 1] - rs;
+  if (len > STAR_MAX_ROW) return;
+  const int32_t* cols = m.col_idx + rs;
+  auto coord = [&](int64_t j) {
+    const float4 h = m.xyz_hi[j], l = m.xyz_lo[j];
+    return V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+  };
+  auto vel = [&](int64_t j) {
+    const V3<float> u = load_vec<float>(f.u, j);
+    return V3<double>{u.x, u.y, u.z};
+  };
+  // even permutations of (0,1,2,3) that bring vertex a to the front
+  const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
+  double acc[STAR_MAX_ROW][4];
+  for (int q = 0; q < len; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
+  const V3<double> xi = coord(i), ui = vel(i);
+  double detsum = 0.0;
+  int dpos = 0;
+  for (int q = 0; q < len; ++q)
+    if (cols[q] == i) dpos = q;
+  for (int32_t t = ptr[r]; t < ptr[r + 1]; ++t) {
+    const int64_t e = inc[t] >> 2;
+    const int a = (int)(inc[t] & 3u);
+    const int4 v4 = m.lnods[e];
+    const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+    int pos[3];
+    V3<double> d[3], u[3];
+    for (int b = 0; b < 3; ++b) {
+      const int j = v[EVEN[a][b]];
+      int lo = 0, hi = len - 1;  // position of j in the row (columns ascending)
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cols[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      pos[b] = lo;
+      d[b] = sub(coord(j), xi);
+      u[b] = vel(j);
+    }
+    const V3<double> c[3] = {cross(d[1], d[2]), cross(d[2], d[0]), cross(d[0], d[1])};
+    const double det = dot(d[0], c[0]);
+    const V3<double> ci{-(c[0].x + c[1].x + c[2].x), -(c[0].y + c[1].y + c[2].y), -(c[0].z + c[1].z + c[2].z)};
+    const double kv = f.kmu / det;
+    const V3<double> w3{f.kc * (2.0 * ui.x + u[0].x + u[1].x + u[2].x) + kv * ci.x,
+                        f.kc * (2.0 * ui.y + u[0].y + u[1].y + u[2].y) + kv * ci.y,
+                        f.kc * (2.0 * ui.z + u[0].z + u[1].z + u[2].z) + kv * ci.z};
+    for (int b = 0; b < 3; ++b) {
+      acc[pos[b]][0] += dot(w3, c[b]);
+      acc[pos[b]][1] += ci.x;
+      acc[pos[b]][2] += ci.y;
+      acc[pos[b]][3] += ci.z;
+    }
+    detsum += det;
+  }
+  // lumped RHS and nodal sums
+  const V3<double> un = [&] {
+    if constexpr (P == NSI_FP64) return load_vec<double>(f.un, i);
+    else {
+      const V3<float> w = load_vec<float>(f.un, i);
+      return V3<double>{w.x, w.y, w.z};
+    }
+  }();
+  Out* Rh = static_cast<Out*>(rhs);
+  Rh[i] = (Out)(f.kmass * detsum * un.x);
+  Rh[m.n + i] = (Out)(f.kmass * detsum * un.y);
+  Rh[2 * m.n + i] = (Out)(f.kmass * detsum * un.z);
+  if constexpr (MODE == 2) {
+    static_cast<Out*>(dt_rho)[i] = (Out)(f.kmass * detsum);
+    static_cast<Out*>(mass_rho)[i] = (Out)(kmr * detsum);
+  }
+  if constexpr (MODE == 0) {
+    // diagonal from the partition of unity, as in the row gather
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < len; ++q)
+      if (q != dpos)
+        for (int k = 0; k < 4; ++k) s[k] += acc[q][k];
+    acc[dpos][0] = f.kmass * detsum - s[0];
+    for (int k = 1; k < 4; ++k) acc[dpos][k] = s[k] / 3.0;
+    Out* Ao = static_cast<Out*>(A) + rs;
+    Out* Go = static_cast<Out*>(G) + rs;
+    for (int q = 0; q < len; ++q) {
+      Ao[q] = (Out)acc[q][0];
+      for (int d = 0; d < 3; ++d) Go[d * m.nnz + q] = (Out)(-acc[q][d + 1] / 24.0);
+    }
+  }
+}
+
 // ------------------------------------------------------ edge-fan kernel ---
 // One thread per CSR entry (i, j) of a block of whole rows.  An off-diagonal
 // entry walks the ring of nodes k_0 .. k_{r-1} around the edge (i, j): the
@@ -1780,8 +1885,33 @@ static nsi_status set_gather_smem() {
   return NSI_OK;
 }
 
+// after an assembly or time step in a mixed mode: the rows listed at create
+// for badly shaped elements, recomputed in double (nothing if there are none)
 template <int P>
-static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s) {
+static nsi_status fix_exact_rows(NsiHandle* h, const FieldView& f, int mode, void* A, void* G, void* rhs,
+                                 void* dt_rho, void* mass_rho, double kmr, cudaStream_t s) {
+  if constexpr (P == NSI_FP64) {
+    return NSI_OK;
+  } else {
+    if (h->exact_rows == 0) return NSI_OK;
+    const MeshView m = view_of(h);
+    const int blk = 64;
+    const int64_t grid = (h->exact_rows + blk - 1) / blk;
+    if (mode == 0)
+      exact_rows_kernel<P, 0><<<grid, blk, 0, s>>>(m, f, A, G, rhs, dt_rho, mass_rho, kmr, h->exact_list,
+                                                  h->exact_ptr, h->exact_inc, h->exact_rows);
+    else if (mode == 1)
+      exact_rows_kernel<P, 1><<<grid, blk, 0, s>>>(m, f, A, G, rhs, dt_rho, mass_rho, kmr, h->exact_list,
+                                                  h->exact_ptr, h->exact_inc, h->exact_rows);
+    else
+      exact_rows_kernel<P, 2><<<grid, blk, 0, s>>>(m, f, A, G, rhs, dt_rho, mass_rho, kmr, h->exact_list,
+                                                  h->exact_ptr, h->exact_inc, h->exact_rows);
+    return check_launch("exact_rows_kernel");
+  }
+}
+
+template <int P>
+static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s) {
   const MeshView m = view_of(h);
   const int blk = 256;
   if (mode == NSI_SCATTER_ATOMIC) {
@@ -1849,6 +1979,13 @@ static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o,
   return check_launch("gather_kernel");
 }
 
+template <int P>
+static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s) {
+  nsi_status st = assemble_core_p<P>(h, f, o, mode, s);
+  if (st) return st;
+  return fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
+}
+
 static nsi_status check_call(const NsiHandle* h, const NsiFields* f, const NsiOutputs* o) {
   if (!h || !f || !o) return fail(NSI_ERR_INVALID_ARG, "handle, fields or outputs is NULL");
   for (int k = 0; k < 3; ++k)
@@ -1909,7 +2046,9 @@ static nsi_status step_p(NsiHandle* h, const FieldView& f, const StepView& o, cu
   if (h->debug) step_kernel<P, NODAL, true><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
   else step_kernel<P, NODAL, false><<<h->plan.n_blocks, R, smem, s>>>(m, f, o, lay);
   if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
-  return check_launch("step_kernel");
+  st = check_launch("step_kernel");
+  if (st) return st;
+  return fix_exact_rows<P>(h, f, NODAL ? 2 : 1, nullptr, nullptr, o.rhs, o.dt_rho, o.mass_rho, o.kmr, s);
 }
 
 static nsi_status step_dispatch(NsiHandle* h, const NsiFields* f, const StepView& o, bool nodal, cudaStream_t s) {
@@ -1930,8 +2069,22 @@ static nsi_status step_dispatch(NsiHandle* h, const NsiFields* f, const StepView
 }
 
 template <int P>
+static nsi_status batched_core_p(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os, int count,
+                                 cudaStream_t s);
+
+template <int P>
 static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os, int count,
                             cudaStream_t s) {
+  nsi_status st = batched_core_p<P>(hs, fs, os, count, s);
+  for (int k = 0; k < count && !st; ++k)
+    st = fix_exact_rows<P>(hs[k], fields_of(&fs[k]), 0, os[k].A_val, os[k].G_val, os[k].rhs, nullptr, nullptr, 0.0,
+                           s);
+  return st;
+}
+
+template <int P>
+static nsi_status batched_core_p(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os, int count,
+                                 cudaStream_t s) {
   static BatchArgs args;  // host staging of the by-value kernel argument
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
@@ -2085,7 +2238,9 @@ static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const Out
   const int R = h->plan.rows_per_block;
   const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
   gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay, 0);
-  return check_launch("gather_kernel (no-alloc)");
+  nsi_status st2 = check_launch("gather_kernel (no-alloc)");
+  if (st2) return st2;
+  return fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
 }
 
 }  // namespace nsi
@@ -2342,7 +2497,7 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f, const NsiOutputs*
   }
   char* ob = base + ((u_bytes + 255) / 256) * 256;
   NsiOutputs od{ob, ob + osz * h->nnz, ob + osz * 4 * h->nnz};
-  if (resolve_mode(h, NSI_SCATTER_AUTO) == NSI_SCATTER_GATHER && !h->use_fan && h->n > 0) {
+  if (resolve_mode(h, NSI_SCATTER_AUTO) == NSI_SCATTER_GATHER && !h->use_fan && h->n > 0 && h->exact_rows == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");

@@ -229,3 +229,47 @@ def test_bad_meshes_rejected():
     with pytest.raises(nsi.NsiError) as ex:
         nsi.Assembler(coord, np.array([[0, 1, 2, 2]], dtype=np.int32))     # degenerate
     assert ex.value.status == nsi.NSI_ERR_BAD_MESH
+
+
+def _sliver_mesh():
+    """4^3 Kuhn cube with node (2,2,2) moved by 0.499 h along (1,-1,0): every
+    tet stays positive, two become slivers whose |d1||d2||d3| / |det| is about
+    1.1e3 (a float determinant would be off by about that many roundings)."""
+    mesh, u = meshgen.config_mesh(N=4, jitter=0.0, numbering="natural", seed=0)
+    coord = mesh.coord.copy()
+    coord[2 + 5 * (2 + 5 * 2)] += 0.499 * 0.25 * np.array([1.0, -1.0, 0.0])
+    return meshgen.Mesh(coord=coord, lnods=mesh.lnods, N=4), u
+
+
+@pytest.mark.parametrize("precision", ["mixed64", "mixed32"])
+def test_badly_shaped_elements_use_double_determinants(precision):
+    mesh, u = _sliver_mesh()
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter="gather")
+    assert asm.info().exact_rows > 0
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = asm.assemble(ut)
+    torch.cuda.synchronize()
+    rp, ci = (t.cpu().numpy() for t in asm.pattern())
+    _, _, oA, oG, orhs = _oracle(mesh, u, precision)
+    err = errors(rp, A.double().cpu().numpy(), G.double().cpu().numpy(), rhs.double().cpu().numpy(), oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], err
+    # the time-step kernels take the same path for the determinant sums
+    A_static, _ = asm.static_part()
+    A2, rhs2 = asm.assemble_convective(ut, A_static)
+    r3, dtr, mr = asm.nodal(ut)
+    torch.cuda.synchronize()
+    from tests._common import row_scaled_err, vec_scaled_err
+    assert row_scaled_err(rp, A2.double().cpu().numpy(), oA) <= TOL[precision]
+    onr, ondt, onm = oracle.nodal(mesh.coord, mesh.lnods, u.astype(np.float32).astype(np.float64), RHO, DT)
+    for k in range(3):
+        assert vec_scaled_err(rhs2[k].double().cpu().numpy(), orhs[k]) <= TOL[precision]
+        assert vec_scaled_err(r3[k].double().cpu().numpy(), onr[k]) <= TOL[precision]
+    assert vec_scaled_err(mr.double().cpu().numpy(), onm) <= TOL[precision]
+    asm.close()
+
+
+def test_regular_meshes_flag_no_rows():
+    mesh, u = meshgen.config_mesh(N=8, jitter=0.15, numbering="random", seed=91)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="mixed64")
+    assert asm.info().exact_rows == 0
+    asm.close()
