@@ -37,7 +37,7 @@ import numpy as np
 __all__ = [
     "Mesh", "kuhn_cube", "jitter_interior", "renumber", "random_permutation",
     "rcm_permutation", "sinusoid_velocity", "add_noise", "gaussian_weights",
-    "config_mesh", "batch_meshes", "CONFIGS",
+    "config_mesh", "batch_meshes", "delaunay_cube", "CONFIGS",
 ]
 
 # permutations of (x, y, z) in itertools order and their parities
@@ -204,6 +204,33 @@ def config_mesh(name: str = None, *, N: int = None, jitter: float = 0.0, numberi
     elif numbering != "natural":
         raise ValueError(numbering)
     mesh.meta.update(numbering=numbering, seed=seed, noise=noise)
+    return mesh, np.ascontiguousarray(u)
+
+
+def delaunay_cube(m: int = 8, jitter: float = 0.25, seed: int = 5):
+    """(mesh, u): an unstructured mesh of the unit cube, the Delaunay
+    tetrahedralization (scipy / Qhull) of the (m+1)^3 lattice with interior
+    points moved by U[-jitter/m, jitter/m] per coordinate.  Irregular stars
+    (rows of 5..24 entries), holes where flat tets (|volume| <= 1e-9 / m^3,
+    on the unjittered faces) are dropped, and slivers.  Tets are listed with
+    positive orientation (two nodes swapped where the triple product of the
+    edge vectors is negative).  u: the seeded sinusoids, as config_mesh."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    g = np.arange(m + 1, dtype=np.float64) / m
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).copy()
+    inner = np.all((P > 0) & (P < 1), axis=1)
+    P[inner] += rng.uniform(-jitter / m, jitter / m, size=(int(inner.sum()), 3))
+    T = Delaunay(P).simplices.astype(np.int64)
+    X = P[T]
+    vol6 = np.linalg.det(X[:, 1:] - X[:, :1])
+    keep = np.abs(vol6) > 1e-9 / m ** 3
+    T, vol6 = T[keep], vol6[keep]
+    T[vol6 < 0] = T[vol6 < 0][:, [0, 1, 3, 2]]
+    mesh = Mesh(coord=P, lnods=T.astype(np.int32), N=m, meta={"kind": "delaunay_cube", "m": m, "jitter": jitter,
+                                                            "seed": seed})
+    u = sinusoid_velocity(P, rng)
     return mesh, np.ascontiguousarray(u)
 
 

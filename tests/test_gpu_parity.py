@@ -273,3 +273,43 @@ def test_regular_meshes_flag_no_rows():
     asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="mixed64")
     assert asm.info().exact_rows == 0
     asm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("scatter", ["gather", "color", "atomic"])
+def test_delaunay_mesh_parity(precision, scatter):
+    """An unstructured mesh (Delaunay tetrahedralization of a jittered lattice):
+    irregular stars of 5..24 entries, holes (several walks per row), slivers."""
+    mesh, u = meshgen.delaunay_cube(8, 0.25, seed=7)
+    rp, ci, A, G, rhs = _run(mesh, u, precision, scatter)
+    orp, oci, oA, oG, orhs = _oracle(mesh, u, precision)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(ci, oci)
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], (precision, scatter, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_delaunay_mesh_steps(precision):
+    from tests._common import row_scaled_err, vec_scaled_err
+
+    mesh, u = meshgen.delaunay_cube(10, 0.3, seed=8)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    if precision != "fp64":
+        assert asm.info().exact_rows > 0  # the slivers' rows
+    ut = torch.as_tensor(u.T.copy())
+    A_static, _ = asm.static_part()
+    A, rhs = asm.assemble_convective(ut, A_static)
+    r3, dtr, mr = asm.nodal(ut)
+    torch.cuda.synchronize()
+    rp = asm.pattern()[0].cpu().numpy()
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    _, _, oA, _, orhs = oracle.assemble(mesh.coord, mesh.lnods, uo, None, RHO, MU, DT)
+    onr, ondt, onm = oracle.nodal(mesh.coord, mesh.lnods, uo, RHO, DT)
+    assert row_scaled_err(rp, A.double().cpu().numpy(), oA) <= TOL[precision]
+    for k in range(3):
+        assert vec_scaled_err(rhs[k].double().cpu().numpy(), orhs[k]) <= TOL[precision]
+        assert vec_scaled_err(r3[k].double().cpu().numpy(), onr[k]) <= TOL[precision]
+    assert vec_scaled_err(dtr.double().cpu().numpy(), ondt) <= TOL[precision]
+    assert vec_scaled_err(mr.double().cpu().numpy(), onm) <= TOL[precision]
+    asm.close()
