@@ -194,12 +194,6 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename T>
-__device__ __forceinline__ void cp_async_t(T* dst, const T* src) {
-  if constexpr (sizeof(T) == 8) cp_async8(dst, src);
-  else cp_async4(dst, src);
-}
-
 // ---------------------------------------------------------- node records ---
 // One record per node, rebuilt every call from the handle's coordinates and
 // the caller's velocities, so that the row-gather kernel fetches a neighbour
