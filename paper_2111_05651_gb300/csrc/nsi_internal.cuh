@@ -254,25 +254,6 @@ __device__ __forceinline__ long long f32_to_f64_bits(float f) {
   return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
-// double nearest to hi + lo for a compensated pair with |lo| <= ulp_float(hi)
-// (the result of TwoSum accumulation): the double bits of hi plus lo expressed
-// in units of hi's double ulp, rounded to nearest (one double ulp at most).
-// A normal float hi with biased exponent e has double ulp 2^(e - 179); lo is
-// scaled by the exact power of two 2^(179 - e).  Finite inputs only.
-__device__ __forceinline__ long long pair_to_f64_bits(float hi, float lo) {
-  const unsigned uh = __float_as_uint(hi);
-  const unsigned eh = (uh >> 23) & 0xffu;
-  if (eh < 52u) return f32_to_f64_bits(hi + lo);  // zero, subnormal or |hi| < 2^-75: the float sum
-  const unsigned hi32 = (uh & 0x80000000u) | ((eh + 896u) << 20) | ((uh & 0x7fffffu) >> 3);
-  const long long bits = (long long)(((unsigned long long)hi32 << 32) | (uh << 29));
-  int k = __float2int_rn(lo * __uint_as_float((306u - eh) << 23));
-  // hi an exact power of two and lo of opposite sign: the sum lies in the binade
-  // below, whose ulp is half as large
-  const unsigned ul = __float_as_uint(lo);
-  if ((uh & 0x7fffffu) == 0u && ((uh ^ ul) & 0x80000000u)) k *= 2;
-  // hi's sign decides the direction of the integer step on the magnitude bits
-  return (uh & 0x80000000u) ? bits - (long long)k : bits + (long long)k;
-}
 
 // error-free sum: s + e == a + b exactly (Knuth's TwoSum, 6 float ops)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -348,14 +348,45 @@ struct Acc<NSI_MIXED_F32_ACC64> {
 
 __device__ __forceinline__ void store_acc(double* p, const Acc<NSI_FP64>& a) { *p = a.v; }
 __device__ __forceinline__ void store_acc(float* p, const Acc<NSI_MIXED_F32_ACC32>& a) { *p = a.v; }
-// the double nearest hi + lo: the pair is renormalised first (Fast2Sum, so
-// that |lo| <= ulp(hi)/2), then the double is built from its bits
+// The double nearest hi + lo for a renormalised float pair (|lo| <= ulp(hi) /
+// 2) with a finite hi, without branches: the double of |hi| from its bits, lo
+// (with hi's sign taken out) added as an integer k of the double's units in
+// the last place (|k| <= 2^28), hi's sign set last.  When |hi| is a power of
+// two and the sum lies below it, k counts the half-size units of the binade
+// below.  Zero gives zero; a tiny |hi| (below 2^-75, where the scale of k would
+// leave the float range) is handled at 2^100 times its size, the exponent
+// taken back in the result.  Infinite and NaN values are the callers' (a test
+// for them here costs the write-out loop several percent).
+__device__ __forceinline__ double normalised_pair_double(float hi, float lo) {
+  const unsigned u0 = __float_as_uint(hi);
+  const bool tiny = ((u0 >> 23) & 0xffu) < 52u;
+  const float sc = tiny ? 0x1p100f : 1.0f;
+  const float h2 = hi * sc, l2 = lo * sc;  // exact
+  const unsigned uh = __float_as_uint(h2);
+  const unsigned eh = (uh >> 23) & 0xffu;
+  const float ls = __uint_as_float(__float_as_uint(l2) ^ (uh & 0x80000000u));
+  const unsigned below = ((uh << 9) == 0u && ls < 0.0f) ? 1u : 0u;
+  const int k = __float2int_rn(ls * __uint_as_float((306u + below - eh) << 23));
+  const unsigned long long mag =
+      ((unsigned long long)(uh & 0x7fffffffu) << 29) + ((tiny ? 796ull : 896ull) << 52);
+  const unsigned long long r = (mag + (unsigned long long)(long long)k) | ((unsigned long long)(uh & 0x80000000u) << 32);
+  return __longlong_as_double((u0 << 1) == 0u ? (long long)((unsigned long long)(u0 & 0x80000000u) << 32)
+                                              : (long long)r);
+}
+// an infinite or NaN accumulator (hi) as a double of the same class
+__device__ __forceinline__ double nonfinite_double(float hi) { return __longlong_as_double(f32_to_f64_bits(hi)); }
+// true if the exponent bits of x are all ones (infinite or NaN)
+__device__ __forceinline__ bool nonfinite_bits(float x) { return (__float_as_uint(x) | 0x807fffffu) == 0xffffffffu; }
+// the double nearest hi + lo of a pair with a finite hi: renormalised first
+// (Fast2Sum)
 __device__ __forceinline__ double pair_double(float hi, float lo) {
   const float s = hi + lo;
   const float l = lo - (s - hi);
-  return __longlong_as_double(pair_to_f64_bits(s, l));
+  return normalised_pair_double(s, l);
 }
-__device__ __forceinline__ void store_acc(double* p, const Acc<NSI_MIXED_F32_ACC64>& a) { *p = pair_double(a.hi, a.lo); }
+__device__ __forceinline__ void store_acc(double* p, const Acc<NSI_MIXED_F32_ACC64>& a) {
+  *p = nonfinite_bits(a.hi) ? nonfinite_double(a.hi) : pair_double(a.hi, a.lo);
+}
 
 template <typename T>
 struct alignas(4 * sizeof(T)) T4 {
@@ -367,7 +398,7 @@ struct alignas(2 * sizeof(T)) T2 {
 };
 
 // Accumulators of the block's slots in shared memory: the A value and the
-// unscaled pressure-gradient sums (sum of c_i) of each entry.  A slot is only
+// pressure-gradient values (sums of -c_i / 24) of each entry.  A slot is only
 // touched by the thread owning its row until the final write-out, so no
 // atomics are needed.  add3() updates three DISTINCT slots (the three other
 // nodes of one element sit at three different positions of the row), so all
@@ -389,7 +420,7 @@ __device__ __forceinline__ void two_sum2(float2& h, float2& l, float2 x) {
   l = add2(l, e);
 }
 
-// Float slots hold (sum c_i x, sum c_i y, sum c_i z, A): the two halves are
+// Float slots hold (G_x, G_y, G_z, A): the two halves are
 // the pairs (G_x, G_y) and (G_z, A) of the paired updates.
 template <>
 struct AccSmem<NSI_MIXED_F32_ACC32> {
@@ -420,11 +451,10 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>* r) {
     a[k] = make_float4(r[1].v, r[2].v, r[3].v, r[0].v);
   }
-  // finished value of component C (0: A, 1..3: G_x..G_z) of slot k
-  template <int C>
-  __device__ __forceinline__ float value(int k, float kg) const {
+  // finished values (A, G_x, G_y, G_z) of slot k
+  __device__ __forceinline__ T4<float> values(int k) const {
     const float4 v = a[k];
-    return C == 0 ? v.w : kg * (C == 1 ? v.x : C == 2 ? v.y : v.z);
+    return {v.w, v.x, v.y, v.z};
   }
 };
 template <>
@@ -452,35 +482,38 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     two_sum2(s.hg, s.lg, gxy);
     two_sum2(s.hr, s.lr, gz_a);
   }
+  // (compensated sums on the float2 lanes (G_x, G_y) and (G_z, A))
   __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
+    float2 hg = make_float2(0.f, 0.f), lg = hg, hr = hg, lr = hg;
     for (int q = 0, k = t; q < len; ++q, k += R) {
       if (k == kd) continue;
       const float4 h = hi[k], l = lo[k];
-      r[0].add(h.w); r[1].add(h.x); r[2].add(h.y); r[3].add(h.z);
-      r[0].lo += l.w; r[1].lo += l.x; r[2].lo += l.y; r[3].lo += l.z;
+      two_sum2(hg, lg, make_float2(h.x, h.y));
+      two_sum2(hr, lr, make_float2(h.z, h.w));
+      lg = add2(lg, make_float2(l.x, l.y));
+      lr = add2(lr, make_float2(l.z, l.w));
     }
+    r[0].hi = hr.y; r[0].lo = lr.y;
+    r[1].hi = hg.x; r[1].lo = lg.x;
+    r[2].hi = hg.y; r[2].lo = lg.y;
+    r[3].hi = hr.x; r[3].lo = lr.x;
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>* r) {
     hi[k] = make_float4(r[1].hi, r[2].hi, r[3].hi, r[0].hi);
     lo[k] = make_float4(r[1].lo, r[2].lo, r[3].lo, r[0].lo);
   }
   // (leading, error) pairs of one half of slot k: half 0 gives G_x and G_y,
-  // half 1 gives G_z and A.  The pressure-gradient sums are scaled by kg with
-  // the product error of the leading part kept.
-  __device__ __forceinline__ float4 pairs(int k, int half, float kg) const {
+  // half 1 gives G_z and A
+  __device__ __forceinline__ float4 pairs(int k, int half) const {
     const float2 h = reinterpret_cast<const float2*>(hi)[2 * k + half];
     const float2 l = reinterpret_cast<const float2*>(lo)[2 * k + half];
-    const float p0 = kg * h.x;
-    const float2 g0 = make_float2(p0, fmaf(kg, h.x, -p0) + kg * l.x);
-    if (half == 1) return make_float4(g0.x, g0.y, h.y, l.y);
-    const float p1 = kg * h.y;
-    return make_float4(g0.x, g0.y, p1, fmaf(kg, h.y, -p1) + kg * l.y);
+    return make_float4(h.x, l.x, h.y, l.y);
   }
 };
 template <>
 struct AccSmem<NSI_FP64> {
-  T2<double>* __restrict__ a0;  // A, sum c_i x
-  T2<double>* __restrict__ a1;  // sum c_i y, sum c_i z
+  T2<double>* __restrict__ a0;  // A, G_x
+  T2<double>* __restrict__ a1;  // G_y, G_z
   __device__ __forceinline__ AccSmem(unsigned char* p, size_t N)
       : a0(reinterpret_cast<T2<double>*>(p)), a1(reinterpret_cast<T2<double>*>(p) + N) {}
   __device__ __forceinline__ void zero(int k) {
@@ -488,7 +521,7 @@ struct AccSmem<NSI_FP64> {
     a1[k] = {0.0, 0.0};
   }
   struct Slot {
-    T2<double> x, y;  // (A, sum c_i x), (sum c_i y, sum c_i z)
+    T2<double> x, y;  // (A, G_x), (G_y, G_z)
   };
   __device__ __forceinline__ Slot load1(int k) const { return {a0[k], a1[k]}; }
   __device__ __forceinline__ void store1(int k, const Slot& v) {
@@ -509,12 +542,9 @@ struct AccSmem<NSI_FP64> {
     a0[k] = {r[0].v, r[1].v};
     a1[k] = {r[2].v, r[3].v};
   }
-  template <int C>
-  __device__ __forceinline__ double value(int k, double kg) const {
-    if (C == 0) return a0[k].x;
-    if (C == 1) return kg * a0[k].y;
-    if (C == 2) return kg * a1[k].x;
-    return kg * a1[k].y;
+  __device__ __forceinline__ T4<double> values(int k) const {
+    const T2<double> x = a0[k], y = a1[k];
+    return {x.x, x.y, y.x, y.y};
   }
 };
 
@@ -541,8 +571,9 @@ __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 // Jacobian, calculate_cartesian_derivatives, for the order (p, q, c)),
 // det = d_p . c_p and c_i = -(c_p + c_q + c_c), the element adds
 //   A(i,x) += w . c_x  (x = p, q, c),  w = rho/120 (2 u_i + u_p + u_q + u_c) + mu/(6 det) c_i
-// and c_i to the three pressure-gradient sums and det to the lumped mass sum
-// (scaled at write-out).  For the order (p, q, c) an odd permutation of the
+// -c_i / 24 (= -|T| grad N_i / 4, the element's G(i, x)) to the three
+// pressure-gradient values and det to the lumped mass sum (scaled after the
+// walk).  For the order (p, q, c) an odd permutation of the
 // element's own, det and every cofactor change sign, w does not, so every
 // contribution is multiplied by -1.  c_c is carried from the previous step:
 // after p leaves, the window (c, q) has d_c x d_q = -c_p; after q leaves,
@@ -572,6 +603,7 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
                                          typename Prec<P>::T kmu, Acc<P>& detsum, unsigned* err) {
   using T = typename Prec<P>::T;
   using Node = WalkNode<T, typename AccSmem<P>::Slot>;
+  constexpr T kg = T(-1.0 / 24.0);  // the pressure-gradient sums are accumulated scaled
   if (nsteps <= 0) return;
   if (DEBUG) {
     bool ok = true;
@@ -604,8 +636,9 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
         const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
                        kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
                        kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
-        const T f = (w & WALK_NEG) ? T(-1) : T(1);  // orientation
-        const T gx = f * ci.x, gy = f * ci.y, gz = f * ci.z;
+        const bool neg = (w & WALK_NEG) != 0u;  // orientation
+        const T f = neg ? T(-1) : T(1), fg = neg ? -kg : kg;
+        const T gx = fg * ci.x, gy = fg * ci.y, gz = fg * ci.z;
         AccSmem<P>::update1(p.v, f * dot(w3, cp), gx, gy, gz);
         AccSmem<P>::update1(q.v, f * dot(w3, cq), gx, gy, gz);
         AccSmem<P>::update1(c.v, -f * dot(w3, m), gx, gy, gz);
@@ -619,12 +652,14 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
       const V3<float> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
                          kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
                          kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
-      const float f = elem ? ((w & WALK_NEG) ? -1.0f : 1.0f) : 0.0f;  // orientation, or 0
-      const float2 ff = make_float2(f, f);
-      const float2 gxy = __fmul2_rn(make_float2(ci.x, ci.y), ff);
+      const bool neg = (w & WALK_NEG) != 0u;
+      const float f = elem ? (neg ? -1.0f : 1.0f) : 0.0f;  // orientation, or 0
+      const float fg = elem ? (neg ? -kg : kg) : 0.0f;
+      const float2 gg = make_float2(fg, fg), ff = make_float2(fg, f);
+      const float2 gxy = __fmul2_rn(make_float2(ci.x, ci.y), gg);
       AccSmem<P>::add(p.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cp)), ff));
       AccSmem<P>::add(q.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cq)), ff));
-      AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(f, -f)));
+      AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(fg, -f)));
       detsum.add(f * det);
     }
     if (w & WALK_EVQ) {
@@ -819,7 +854,6 @@ __device__ __forceinline__ void gather_compute(const MeshView& m, const FieldVie
   const T kc = kc_of<T>(f);
   const T kmu = kmu_of<T>(f);
   const T kmass = kmass_of<T>(f);
-  const T kg = (T)(-1.0 / 24.0);
   Acc<P> detsum;
   detsum.zero();
   if (t < nrows) {
@@ -888,7 +922,6 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
   using Out = typename Prec<P>::Out;
   const int R = b.R, t = b.t, nrows = b.nrows, L = b.L, len = b.len, lb = b.lb;
   const int32_t base = b.base;
-  const T kg = (T)(-1.0 / 24.0);
   // phase 3: the block's contiguous slice of A and G.  Every thread moves its
   // own row's finished values into CSR order (nb0 reused as staging), then the
   // block streams the slice out coalesced.
@@ -901,10 +934,11 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
     if (t < nrows) {
 #pragma unroll 4
       for (int q = 0, k = t; q < len; ++q, k += R) {
-        stage[lb + q] = acc.template value<0>(k, kg);
-        stage[L + lb + q] = acc.template value<1>(k, kg);
-        stage[2 * L + lb + q] = acc.template value<2>(k, kg);
-        stage[3 * L + lb + q] = acc.template value<3>(k, kg);
+        const T4<Out> v = acc.values(k);
+        stage[lb + q] = v.x;
+        stage[L + lb + q] = v.y;
+        stage[2 * L + lb + q] = v.z;
+        stage[3 * L + lb + q] = v.w;
       }
     }
     __syncthreads();
@@ -920,24 +954,37 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
     // in CSR order, then the block converts them while streaming them out
     // coalesced (the conversions spread evenly over the threads)
     float2* pairs = reinterpret_cast<float2*>(smem + lay.nb0());
+    bool nonfinite = false;  // an infinite or NaN value among the thread's (rare; fixed after the loop)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       if (t < nrows) {
 #pragma unroll 4
         for (int q = 0; q < len; ++q) {
-          const float4 pr = acc.pairs(q * R + t, half, kg);
+          const float4 pr = acc.pairs(q * R + t, half);
           pairs[lb + q] = make_float2(pr.x, pr.y);
           pairs[L + lb + q] = make_float2(pr.z, pr.w);
+          nonfinite |= nonfinite_bits(pr.x) | nonfinite_bits(pr.z);
         }
       }
-      __syncthreads();
+      const bool fix = __syncthreads_or(nonfinite);
       // half 0: G_x, G_y; half 1: G_z, A
       Out* d0 = half ? dst[3] : dst[1];
       Out* d1 = half ? dst[0] : dst[2];
       for (int k = t; k < L; k += R) {
         const float2 a = pairs[k], b = pairs[L + k];
-        d0[k] = pair_double(a.x, a.y);
-        d1[k] = pair_double(b.x, b.y);
+        // both pairs renormalised at once (Fast2Sum on the float2 lanes, so
+        // that |error| <= ulp(leading) / 2), then converted
+        const float2 h = make_float2(a.x, b.x), l = make_float2(a.y, b.y);
+        const float2 sh = add2(h, l);
+        const float2 sl = sub2(l, sub2(sh, h));
+        d0[k] = normalised_pair_double(sh.x, sl.x);
+        d1[k] = normalised_pair_double(sh.y, sl.y);
+      }
+      if (fix) {  // block-uniform: infinite and NaN values keep their class
+        for (int k = t; k < L; k += R) {
+          if (nonfinite_bits(pairs[k].x)) d0[k] = nonfinite_double(pairs[k].x);
+          if (nonfinite_bits(pairs[L + k].x)) d1[k] = nonfinite_double(pairs[L + k].x);
+        }
       }
       if (half == 0) __syncthreads();
     }
@@ -1195,11 +1242,19 @@ __device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f,
     cp_async_wait_all();
     if constexpr (P == NSI_MIXED_F32_ACC64) {
       float2* stage = reinterpret_cast<float2*>(smem + lay.nb0());
+      bool nonfinite = false;  // as in the assembly's write-out
       if (t < b.nrows)
-        for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
-      __syncthreads();
+        for (int q = 0; q < b.len; ++q) {
+          const float2 v = acc.load1(q * R + t);
+          stage[b.lb + q] = v;
+          nonfinite |= nonfinite_bits(v.x);
+        }
+      const bool fix = __syncthreads_or(nonfinite);
 #pragma unroll 2
       for (int k = t; k < b.L; k += R) A[k] = stat[k] + pair_double(stage[k].x, stage[k].y);
+      if (fix)
+        for (int k = t; k < b.L; k += R)
+          if (nonfinite_bits(stage[k].x)) A[k] = stat[k] + nonfinite_double(stage[k].x);
     } else {
       Out* stage = reinterpret_cast<Out*>(smem + lay.nb0());
       if (t < b.nrows)

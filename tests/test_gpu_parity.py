@@ -71,6 +71,72 @@ def test_parity_vs_oracle(case, precision, scatter):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64"])
+@pytest.mark.parametrize("scatter", ["gather", "color", "atomic"])
+def test_integer_valued_assembly_is_exact(precision, scatter):
+    """Integer lattice (unit Kuhn tets, det = 1), integer velocities below 2^19,
+    rho = 120 (rho/120 = 1), mu = 0 and dt = 5 / 2^20 (lumped mass rho|T|/(4 dt)
+    = 2^20 per element): every element term of A and of the RHS is an integer
+    exact in float (the convection terms below 2^22), while the diagonal
+    entries, the lumped mass minus the row's other entries, need up to 26 bits.
+    FP64 and the compensated float-pair sums of mixed64 with their conversion
+    to double must then give the exact integers: the oracle's values rounded to
+    the nearest integer (its 4-point quadrature leaves them within 1e-3 of
+    one).  The cached-geometry time step (A_static + C(u)) must give them too."""
+    N = 7
+    mesh, _ = meshgen.config_mesh(N=N, numbering="random", seed=86)
+    coord = np.rint(mesh.coord * N)
+    rng = np.random.default_rng(87)
+    u = rng.integers(-2**19, 2**19, size=(mesh.n_nodes, 3)).astype(np.float64)
+    un = rng.integers(-2**10, 2**10, size=(mesh.n_nodes, 3)).astype(np.float64)
+    rho, mu, dt = 120.0, 0.0, 5.0 / 2**20
+    _, _, oA, _, orhs = oracle.assemble(coord, mesh.lnods, u, un, rho, mu, dt)
+    iA, irhs = np.rint(oA), np.rint(orhs)
+    assert np.abs(oA - iA).max() < 1e-3 and np.abs(orhs - irhs).max() < 1e-3
+    assert (iA.astype(np.float32).astype(np.float64) != iA).sum() >= 10  # entries past float's integers
+    asm = nsi.Assembler(coord, mesh.lnods, precision=precision, scatter=scatter)
+    ut, unt = torch.as_tensor(u.T.copy()), torch.as_tensor(un.T.copy())
+    A, _, rhs = asm.assemble(ut, unt, rho=rho, mu=mu, dt=dt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(A.cpu().numpy(), iA)
+    np.testing.assert_array_equal(rhs.cpu().numpy(), irhs)
+    if scatter == "gather":
+        A_static, _ = asm.static_part(rho=rho, mu=mu, dt=dt)
+        A2, rhs2 = asm.assemble_convective(ut, A_static, u_n=unt, rho=rho, mu=mu, dt=dt)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(A2.cpu().numpy(), iA)
+        np.testing.assert_array_equal(rhs2.cpu().numpy(), irhs)
+    asm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf], ids=["nan", "inf"])
+def test_nonfinite_velocity_propagates(precision, bad):
+    """A NaN or infinite velocity at one node makes the A entries and the RHS
+    of that node's row non-finite, in the assembly and in the cached-geometry
+    step; rows outside its neighbourhood and G (velocity-free) stay finite."""
+    mesh, u = meshgen.config_mesh(N=6, jitter=0.1, numbering="random", seed=88)
+    b = int(np.argmin(np.abs(mesh.coord - 0.5).sum(1)))  # an interior node
+    u = u.copy()
+    u[b, 1] = bad
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = (x.double().cpu().numpy() for x in asm.assemble(ut))
+    A_static, _ = asm.static_part()
+    A2, rhs2 = (x.double().cpu().numpy() for x in asm.assemble_convective(ut, A_static))
+    rp, ci = (x.cpu().numpy() for x in asm.pattern())
+    asm.close()
+    near = np.zeros(mesh.n_nodes, dtype=bool)
+    near[ci[rp[b]:rp[b + 1]]] = True  # b and its neighbours
+    far = np.repeat(~near, np.diff(rp))
+    for a, r in ((A, rhs), (A2, rhs2)):
+        assert not np.isfinite(a[rp[b]:rp[b + 1]]).all()
+        assert not np.isfinite(r[1, b])
+        assert np.isfinite(a[far]).all()
+        assert np.isfinite(r[:, ~near]).all()
+    assert np.isfinite(G).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64"])
 def test_separate_rhs_velocity(precision):
     mesh, u = meshgen.config_mesh(N=5, jitter=0.1, numbering="random", seed=40)
     un = np.random.default_rng(41).standard_normal(u.shape)
