@@ -2325,8 +2325,16 @@ static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOut
   Out* hA = static_cast<Out*>(o->A_val);
   Out* hG = static_cast<Out*>(o->G_val);
   Out* hR = static_cast<Out*>(o->rhs);
+  // the link, not the kernel, bounds the call: a small first chunk starts the
+  // copies early, later chunks grow (the kernel runs ahead of the copies)
+  static_assert(C == 8, "chunk fractions are listed for 8 chunks");
+  const double frac[C + 1] = {0.0, 1.0 / 64, 1.0 / 16, 3.0 / 16, 5.0 / 16, 0.5, 11.0 / 16, 27.0 / 32, 1.0};
+  auto bound = [&](int c) {
+    return chunks == C ? (int64_t)((double)nb * frac[c]) : nb * c / chunks;
+  };
   for (int c = 0; c < chunks; ++c) {
-    const int64_t b0 = nb * c / chunks, b1 = nb * (c + 1) / chunks;
+    const int64_t b0 = bound(c), b1 = c + 1 == chunks ? nb : bound(c + 1);
+    if (b1 <= b0) continue;
     if (h->debug) gather_kernel<P, true><<<b1 - b0, R, smem, s>>>(m, fv, ov, lay, b0);
     else gather_kernel<P, false><<<b1 - b0, R, smem, s>>>(m, fv, ov, lay, b0);
     st = check_launch("gather_kernel (host chunk)");

@@ -226,9 +226,37 @@ def test_batched_equals_single():
             assert torch.equal(x, y)
 
 
-def test_host_end_to_end_matches_device():
+@pytest.mark.parametrize("pinned", ["all", "none", "inputs"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_host_end_to_end_matches_device(precision, pinned):
+    """nsi_assemble_host gives the device call's bits, with every buffer pinned
+    (the kernels read and write host memory directly) and with pageable
+    buffers or a mix (staged copies)."""
     mesh, u = meshgen.config_mesh(N=6, jitter=0.15, numbering="random", seed=45)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = asm.assemble(ut)
+
+    def host(t, pin):
+        return t.pin_memory() if pin else t
+
+    uh = host(ut.to(asm.vel_dtype), pinned != "none")
+    Ah = host(torch.empty(asm.nnz, dtype=asm.out_dtype), pinned == "all")
+    Gh = host(torch.empty(3, asm.nnz, dtype=asm.out_dtype), pinned == "all")
+    rh = host(torch.empty(3, asm.n, dtype=asm.out_dtype), pinned == "all")
+    asm.assemble_host(uh, Ah, Gh, rh)
+    assert torch.equal(A.cpu(), Ah)
+    assert torch.equal(G.cpu(), Gh)
+    assert torch.equal(rhs.cpu(), rh)
+    asm.close()
+
+
+def test_host_end_to_end_badly_shaped_elements():
+    """The direct host path also runs the double-precision fix-up of the rows
+    of badly shaped elements (on the host buffers)."""
+    mesh, u = _sliver_mesh()
     asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="mixed64")
+    assert asm.info().exact_rows > 0
     ut = torch.as_tensor(u.T.copy())
     A, G, rhs = asm.assemble(ut)
     uh = ut.float().pin_memory()
@@ -236,9 +264,8 @@ def test_host_end_to_end_matches_device():
     Gh = torch.empty(3, asm.nnz, dtype=torch.float64).pin_memory()
     rh = torch.empty(3, asm.n, dtype=torch.float64).pin_memory()
     asm.assemble_host(uh, Ah, Gh, rh)
-    assert torch.equal(A.cpu(), Ah)
-    assert torch.equal(G.cpu(), Gh)
-    assert torch.equal(rhs.cpu(), rh)
+    assert torch.equal(A.cpu(), Ah) and torch.equal(G.cpu(), Gh) and torch.equal(rhs.cpu(), rh)
+    asm.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64"])
