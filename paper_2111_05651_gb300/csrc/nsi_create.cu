@@ -226,17 +226,15 @@ static bool encode_walk(const uint16_t* tri, int m, int dp, std::vector<uint8_t>
     r0 = wp;
     r1 = wq;
     r2 = c;
-    if (evq)  // the leaving node's registers take c
-      wq = c;
-    else
-      wp = c;
+    if (!evq) wp = wq;  // p leaves: q's node moves to p
+    wq = c;             // the newest node is always q
     return true;
   };
   for (size_t pi = 0; pi < paths.size(); ++pi) {
     std::vector<int> path = paths[pi];
     if (pi > 0) {  // flush: dp into both window registers
       emit(dp, false, false, false);
-      emit(dp, false, false, true);
+      emit(dp, false, false, false);
     }
     // first element (x, y, z) in its own order, z on the edge shared with the
     // next element; x must not be a node the flush still holds
@@ -251,7 +249,7 @@ static bool encode_walk(const uint16_t* tri, int m, int dp, std::vector<uint8_t>
       y = P(t0, (c + 2) % 3);
       z = zc;
     }
-    if (x < 0 || !emit(x, false, false, false) || !emit(y, false, false, true)) return false;  // window (x, y)
+    if (x < 0 || !emit(x, false, false, false) || !emit(y, false, false, false)) return false;  // window (x, y)
     for (size_t k = 0; k < path.size(); ++k) {
       const int t = path[k];
       if (!has(t, wp) || !has(t, wq)) return false;

@@ -48,7 +48,7 @@ constexpr double EXACT_RATIO = 16.0;
 constexpr unsigned WALK_POS = 31u;       // bits 0-4: row position of the new node
 constexpr unsigned WALK_ELEM = 1u << 5;  // the step evaluates element (p, q, c)
 constexpr unsigned WALK_NEG = 1u << 6;   // (p, q, c) is an odd permutation of the element's order
-constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves, c takes its place (window (p, c)); else p leaves (window (c, q))
+constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves (next window (p, c)); else p leaves (next window (q, c))
 
 // Edge-fan map: for every off-diagonal CSR entry (i, j), the ring of nodes
 // around the edge (i, j) -- the other two nodes of every element containing

@@ -578,8 +578,9 @@ __device__ __forceinline__ double rcp_fast(double x) {
 // origin.  A window of two neighbours (p, q) stays in registers with their
 // edge vectors, velocities and accumulators; every step brings one node c in
 // from shared memory, evaluates the element (i, p, q, c) if the step says so,
-// then writes back the accumulator of the node that leaves the window and
-// puts c in its registers (the window stays (p, q) in register order).  With
+// then writes back the accumulator of the node that leaves the window; c
+// always becomes q, and p keeps its node or takes q's (one register move of
+// a node per step instead of two selects).  With
 // c_p = d_q x d_c, c_q = d_c x d_p, c_c = d_p x d_q (cofactors of the
 // Jacobian, calculate_cartesian_derivatives, for the order (p, q, c)),
 // det = d_p . c_p and c_i = -(c_p + c_q + c_c), the element adds
@@ -589,8 +590,9 @@ __device__ __forceinline__ double rcp_fast(double x) {
 // walk).  For the order (p, q, c) an odd permutation of the
 // element's own, det and every cofactor change sign, w does not, so every
 // contribution is multiplied by -1.  c_c is carried from the previous step:
-// after p leaves, the window (c, q) has d_c x d_q = -c_p; after q leaves,
-// (p, c) has d_p x d_c = -c_q; m holds c_p or c_q, and c_c = -m.
+// after q leaves, the window (p, c) has d_p x d_c = -c_q; after p leaves,
+// (q, c) has d_q x d_c = c_p; m holds c_q or c_p and c_c = -sg m with sg = 1
+// or -1.
 template <typename T, typename Slot>
 struct WalkNode {
   int k;  // shared-memory slot
@@ -630,6 +632,7 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   Node p = walk_load<P>(kd, nb0, nb1, acc);
   Node q = p;
   V3<T> m{T(0), T(0), T(0)};
+  T sg = T(1);  // c_c = -sg m
   unsigned w = st[0];
   Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
 #pragma unroll 2  // two steps' arithmetic interleave (measured faster)
@@ -644,7 +647,7 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
     if constexpr (P == NSI_FP64) {
       if (elem) {  // (steps that only fill the window come first in a row: warp-uniform)
         const T det = dot(p.d, cp);
-        const V3<T> ci{m.x - cp.x - cq.x, m.y - cp.y - cq.y, m.z - cp.z - cq.z};
+        const V3<T> ci{fma(sg, m.x, -(cp.x + cq.x)), fma(sg, m.y, -(cp.y + cq.y)), fma(sg, m.z, -(cp.z + cq.z))};
         const T kv = kmu * rcp_fast(det);
         const V3<T> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
                        kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
@@ -654,13 +657,13 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
         const T gx = fg * ci.x, gy = fg * ci.y, gz = fg * ci.z;
         AccSmem<P>::update1(p.v, f * dot(w3, cp), gx, gy, gz);
         AccSmem<P>::update1(q.v, f * dot(w3, cq), gx, gy, gz);
-        AccSmem<P>::update1(c.v, -f * dot(w3, m), gx, gy, gz);
+        AccSmem<P>::update1(c.v, -f * sg * dot(w3, m), gx, gy, gz);
         detsum.add(f * det);
       }
     } else {
       // branch-free: a step that only fills the window adds zeros
       const float det = dot(p.d, cp);
-      const V3<float> ci{m.x - cp.x - cq.x, m.y - cp.y - cq.y, m.z - cp.z - cq.z};
+      const V3<float> ci{fmaf(sg, m.x, -(cp.x + cq.x)), fmaf(sg, m.y, -(cp.y + cq.y)), fmaf(sg, m.z, -(cp.z + cq.z))};
       const float kv = kmu * rcp_fast(elem ? det : 1.0f);
       const V3<float> w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x,
                          kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
@@ -672,18 +675,21 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
       const float2 gxy = __fmul2_rn(make_float2(ci.x, ci.y), gg);
       AccSmem<P>::add(p.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cp)), ff));
       AccSmem<P>::add(q.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, cq)), ff));
-      AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(fg, -f)));
+      AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(fg, -f * sg)));
       detsum.add(f * det);
     }
+    // the newest node always enters q; p keeps the older node or takes q's
     if (w & WALK_EVQ) {
       acc.store1(q.k, q.v);
-      q = c;
       m = cq;
+      sg = T(1);
     } else {
       acc.store1(p.k, p.v);
-      p = c;
+      p = q;
       m = cp;
+      sg = T(-1);
     }
+    q = c;
     c = cn;
     w = wn;
   }
@@ -1131,6 +1137,7 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
   Node p = load(kd);
   Node q = p;
   V3<T> m{T(0), T(0), T(0)};
+  T sg = T(1);  // c_c = -sg m
   unsigned w = st[0];
   Node c = load((int)(w & WALK_POS) * R + t);
 #pragma unroll 2
@@ -1146,17 +1153,20 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
                      kc * (u2i.z + p.u.z + q.u.z + c.u.z)};
       AccA<P>::add(p.v, f * dot(w3, cp));
       AccA<P>::add(q.v, f * dot(w3, cq));
-      AccA<P>::add(c.v, -f * dot(w3, m));
+      AccA<P>::add(c.v, -f * sg * dot(w3, m));
     }
+    // as walk_row: the newest node always enters q
     if (w & WALK_EVQ) {
       if constexpr (!NODAL) acc.store1(q.k, q.v);
-      q = c;
       m = cq;
+      sg = T(1);
     } else {
       if constexpr (!NODAL) acc.store1(p.k, p.v);
-      p = c;
+      p = q;
       m = cp;
+      sg = T(-1);
     }
+    q = c;
     c = cn;
     w = wn;
   }

@@ -4,9 +4,9 @@
 // builds every row's star independently (the positions of each incident
 // element's other three nodes, listed as an even permutation), encodes it with
 // the library's own encode_walk, and replays the walk the way the kernel runs
-// it: a window of two nodes in registers, in-place replacement of the node
-// that leaves, orientation from the step byte, the carried cofactor kept
-// negated, the next node's accumulator read BEFORE the leaving node's is
+// it: a window of two nodes in registers (the newest node always enters q, p
+// keeps its node or takes q's), orientation from the step byte, the carried
+// cofactor with its sign, the next node's accumulator read BEFORE the leaving node's is
 // written back (stale reads are simulated).  The replayed row sums (the
 // convection + viscous entries w . c_x, the pressure-gradient sums of c_i and
 // the determinant sum) must equal direct sums over the star in double.
@@ -139,6 +139,7 @@ int main(int argc, char** argv) {
     };
     Node p = load(dp), q = load(dp);
     P3 m{0, 0, 0};
+    double sg = 1.0;  // c_c = -sg m
     unsigned w = out[0];
     Node c = load(w & nsi::WALK_POS);
     const size_t ns = out.size();
@@ -150,14 +151,14 @@ int main(int argc, char** argv) {
       const P3 cp = cross3(q.d, c.d), cq = cross3(c.d, p.d);
       if (w & nsi::WALK_ELEM) {
         const double det = dot3(p.d, cp);
-        const P3 ci{m.x - cp.x - cq.x, m.y - cp.y - cq.y, m.z - cp.z - cq.z};
+        const P3 ci{sg * m.x - cp.x - cq.x, sg * m.y - cp.y - cq.y, sg * m.z - cp.z - cq.z};
         const double kv = kmu / det;
         const P3 w3{kc * (u2i.x + p.u.x + q.u.x + c.u.x) + kv * ci.x, kc * (u2i.y + p.u.y + q.u.y + c.u.y) + kv * ci.y,
                     kc * (u2i.z + p.u.z + q.u.z + c.u.z) + kv * ci.z};
         const double f = (w & nsi::WALK_NEG) ? -1.0 : 1.0;
         p.a += f * dot3(w3, cp);
         q.a += f * dot3(w3, cq);
-        c.a += -f * dot3(w3, m);
+        c.a += -f * sg * dot3(w3, m);
         for (Node* nd : {&p, &q, &c}) {
           nd->gx += f * ci.x;
           nd->gy += f * ci.y;
@@ -165,15 +166,17 @@ int main(int argc, char** argv) {
         }
         sD += f * det;
       }
-      if (w & nsi::WALK_EVQ) {
+      if (w & nsi::WALK_EVQ) {  // q leaves
         store(q);
-        q = c;
         m = cq;
-      } else {
+        sg = 1.0;
+      } else {  // p leaves, q's node moves to p
         store(p);
-        p = c;
+        p = q;
         m = cp;
+        sg = -1.0;
       }
+      q = c;  // the newest node is always q
       if (!last) c = cn;
       w = wn;
     }
