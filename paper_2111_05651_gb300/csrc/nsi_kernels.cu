@@ -621,22 +621,25 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   constexpr T kg = T(-1.0 / 24.0);  // the pressure-gradient sums are accumulated scaled
   if (nsteps <= 0) return;
   if (DEBUG) {
-    bool ok = true;
+    bool ok = nsteps >= 3 && !(st[0] & WALK_ELEM) && !(st[1] & WALK_ELEM);
     for (int s = 0; s < nsteps; ++s) ok &= (int)(st[s] & WALK_POS) < len;
     if (!ok) {
       atomicOr(err, ERR_STAR);
       return;
     }
   }
-  // the window starts on the diagonal slot (edge vector 0, accumulator 0)
-  Node p = walk_load<P>(kd, nb0, nb1, acc);
-  Node q = p;
-  V3<T> m{T(0), T(0), T(0)};
-  T sg = T(1);  // c_c = -sg m
-  unsigned w = st[0];
+  if (nsteps < 3) return;  // (every walk of a row with elements has at least 3 steps)
+  // a row's walk starts with two steps that only fill the window (the
+  // encoder begins the first path that way): their nodes are loaded directly,
+  // with the cofactor the first element carries, c_c = d_p x d_q
+  Node p = walk_load<P>((int)(st[0] & WALK_POS) * R + t, nb0, nb1, acc);
+  Node q = walk_load<P>((int)(st[1] & WALK_POS) * R + t, nb0, nb1, acc);
+  V3<T> m = cross(p.d, q.d);
+  T sg = T(-1);  // c_c = -sg m
+  unsigned w = st[2];
   Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
 #pragma unroll 2  // two steps' arithmetic interleave (measured faster)
-  for (int s = 0; s < nsteps; ++s) {
+  for (int s = 2; s < nsteps; ++s) {
     // the next step's node, in flight while this element is evaluated (never
     // one of p, q, c: the walk is encoded that way; the last step reloads its
     // own node, unused)
@@ -1114,13 +1117,14 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
   using Node = WalkNode<T, typename AccA<P>::Slot>;
   if (nsteps <= 0) return;
   if (DEBUG) {
-    bool ok = true;
+    bool ok = nsteps >= 3 && !(st[0] & WALK_ELEM) && !(st[1] & WALK_ELEM);
     for (int s = 0; s < nsteps; ++s) ok &= (int)(st[s] & WALK_POS) < len;
     if (!ok) {
       atomicOr(err, ERR_STAR);
       return;
     }
   }
+  if (nsteps < 3) return;  // (every walk of a row with elements has at least 3 steps)
   auto load = [&](int k) {
     const T4<T> a = nb0[k];
     Node nd;
@@ -1134,14 +1138,15 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
     return nd;
   };
   const int last = nsteps - 1;
-  Node p = load(kd);
-  Node q = p;
-  V3<T> m{T(0), T(0), T(0)};
-  T sg = T(1);  // c_c = -sg m
-  unsigned w = st[0];
+  // as walk_row: the two filling steps' nodes loaded directly
+  Node p = load((int)(st[0] & WALK_POS) * R + t);
+  Node q = load((int)(st[1] & WALK_POS) * R + t);
+  V3<T> m = cross(p.d, q.d);
+  T sg = T(-1);  // c_c = -sg m
+  unsigned w = st[2];
   Node c = load((int)(w & WALK_POS) * R + t);
 #pragma unroll 2
-  for (int s = 0; s < nsteps; ++s) {
+  for (int s = 2; s < nsteps; ++s) {
     const unsigned wn = st[min(s + 1, last)];
     const Node cn = load((int)(wn & WALK_POS) * R + t);
     const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);

@@ -137,13 +137,19 @@ int main(int argc, char** argv) {
       sY[nd.k] = nd.gy;
       sZ[nd.k] = nd.gz;
     };
-    Node p = load(dp), q = load(dp);
-    P3 m{0, 0, 0};
-    double sg = 1.0;  // c_c = -sg m
-    unsigned w = out[0];
+    // the first two steps only fill the window: the kernel loads their nodes
+    // directly, with the first element's carried cofactor d_p x d_q
+    if (out.size() < 3 || (out[0] & nsi::WALK_ELEM) || (out[1] & nsi::WALK_ELEM)) {
+      std::printf("FAIL row %lld: the walk does not start with two filling steps\n", (long long)i);
+      return 1;
+    }
+    Node p = load(out[0] & nsi::WALK_POS), q = load(out[1] & nsi::WALK_POS);
+    P3 m = cross3(p.d, q.d);
+    double sg = -1.0;  // c_c = -sg m
+    unsigned w = out[2];
     Node c = load(w & nsi::WALK_POS);
     const size_t ns = out.size();
-    for (size_t s = 0; s < ns; ++s) {
+    for (size_t s = 2; s < ns; ++s) {
       const bool last = s + 1 >= ns;
       const unsigned wn = last ? w : out[s + 1];
       Node cn{};
