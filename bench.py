@@ -573,7 +573,8 @@ def run_step(args, world, rank, local):
                           "config": {"workload": WORKLOADS["step100"], "precision": "mixed64",
                                      "l2": "flushed (256 MiB write) before every timed step"},
                           "roofline": {"bound": "hbm", "achieved": m["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                                       "frac": m["achieved_gbs"] / peak, "traffic": None, "kernel": "step_kernel",
+                                       "frac": m["achieved_gbs"] / peak,
+                                       "traffic": read_traffic("step_kernel", "cube100", "mixed64"), "kernel": "step_kernel",
                                        "algorithmic_bytes": m["algorithmic_bytes"], "kernel_ms": m["kernel_ms"],
                                        "peak_source": src},
                           "max_rel_err": m["max_rel_err"], "modes": res}), flush=True)
