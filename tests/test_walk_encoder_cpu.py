@@ -3,7 +3,8 @@
 tests/walk_replay.cu compiles the library's create-time code with a small
 driver: for every row of a mesh it builds the row's star, encodes the walk
 with the library's encode_walk, and replays it the way the kernel runs it
-(window registers, in-place replacement, orientation bits, carried cofactor,
+(window registers with the newest node always in q, the first window loaded
+directly, orientation bits, the carried cofactor and its sign,
 the next node read before the leaving node is written back).  The replayed
 row sums must equal direct sums over the star in double, every element must
 be walked exactly once, and no step may read a node still held in registers.
