@@ -119,8 +119,8 @@ typedef struct {
 } NsiFields;
 
 typedef struct {
-    void* A_val; /* device [nnz], double or float by precision */
-    void* G_val; /* device [3][nnz] */
+    void* A_val; /* device [nnz], double or float by precision (may be NULL when nnz = 0) */
+    void* G_val; /* device [3][nnz] (may be NULL when nnz = 0) */
     void* rhs;   /* device [3][n_nodes] */
 } NsiOutputs;
 
@@ -201,7 +201,8 @@ nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const
  * dt (the viscous part plus the lumped mass) and C(u) the convection term.  G
  * does not change and is not written.  A_static, A_val: device [nnz] of the
  * handle's output type (A_val may alias A_static: every entry is read before
- * it is written, by the same thread); rhs: device [3][n_nodes], overwritten;
+ * it is written, by the same thread; both may be NULL when nnz = 0); rhs:
+ * device [3][n_nodes], overwritten;
  * the velocities in `f` as for nsi_assemble.  Needs the row-gather map
  * (rows of at most 32 entries): NSI_ERR_UNSUPPORTED otherwise.
  */

@@ -2067,7 +2067,8 @@ static nsi_status check_call(const NsiHandle* h, const NsiFields* f, const NsiOu
   if (!h || !f || !o) return fail(NSI_ERR_INVALID_ARG, "handle, fields or outputs is NULL");
   for (int k = 0; k < 3; ++k)
     if (!f->u[k]) return fail(NSI_ERR_INVALID_ARG, "velocity component pointer is NULL");
-  if (!o->A_val || !o->G_val || !o->rhs) return fail(NSI_ERR_INVALID_ARG, "output pointer is NULL");
+  if ((h->nnz > 0 && (!o->A_val || !o->G_val)) || !o->rhs)
+    return fail(NSI_ERR_INVALID_ARG, "output pointer is NULL");
   if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");
   return NSI_OK;
 }
@@ -2416,7 +2417,7 @@ nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const
 
 nsi_status nsi_assemble_convective(NsiHandle* h, const NsiFields* f, const void* A_static, void* A_val, void* rhs,
                                    void* stream) {
-  if (!h || !f || !A_static || !A_val || !rhs) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
+  if (!h || !f || !rhs || (h->nnz > 0 && (!A_static || !A_val))) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
   for (int k = 0; k < 3; ++k)
     if (!f->u[k]) return fail(NSI_ERR_INVALID_ARG, "velocity component pointer is NULL");
   if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");

@@ -178,6 +178,32 @@ def test_single_tet_and_isolated_node():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("scatter", ["gather", "color", "atomic"])
+def test_mesh_without_elements(precision, scatter):
+    """Nodes and no elements: an empty pattern (nnz = 0, NULL A and G are
+    accepted), a zero RHS, and the same from the time-step entry points."""
+    coord = np.random.default_rng(91).standard_normal((7, 3))
+    lnods = np.zeros((0, 4), dtype=np.int32)
+    asm = nsi.Assembler(coord, lnods, precision=precision, scatter=scatter)
+    assert asm.nnz == 0
+    ut = torch.as_tensor(np.random.default_rng(92).standard_normal((3, 7)))
+    A, G, rhs = asm.assemble(ut)
+    torch.cuda.synchronize()
+    assert A.numel() == 0 and G.numel() == 0
+    assert torch.count_nonzero(rhs) == 0
+    rp = asm.pattern()[0].cpu().numpy()
+    assert np.all(rp == 0)
+    if scatter == "gather":
+        A_static, _ = asm.static_part()
+        A2, rhs2 = asm.assemble_convective(ut, A_static)
+        r3, dtr, mr = asm.nodal(ut)
+        torch.cuda.synchronize()
+        assert A2.numel() == 0 and torch.count_nonzero(rhs2) == 0
+        assert torch.count_nonzero(r3) == 0 and torch.count_nonzero(dtr) == 0 and torch.count_nonzero(mr) == 0
+    asm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
 def test_edge_fan_kernel_matches_oracle(precision):
     """The edge-fan variant of the row gather (selected with nsi_set_launch(-1))."""
     for kw in (dict(N=7, jitter=0.15, numbering="random", seed=71), dict(name="cube8")):
@@ -322,6 +348,59 @@ def test_bad_meshes_rejected():
     with pytest.raises(nsi.NsiError) as ex:
         nsi.Assembler(coord, np.array([[0, 1, 2, 2]], dtype=np.int32))     # degenerate
     assert ex.value.status == nsi.NSI_ERR_BAD_MESH
+
+
+def _fan_mesh(m):
+    """m tets around the vertical edge from node 0 (origin) to node m + 1 (top),
+    with a ring of m nodes: rows 0 and m + 1 have m + 2 entries."""
+    ang = 2 * np.pi * np.arange(m) / m
+    coord = np.vstack([[0, 0, 0], np.c_[np.cos(ang), np.sin(ang), np.zeros(m)], [0, 0, 1]]).astype(float)
+    lnods = []
+    for k in range(m):
+        t = [0, 1 + k, 1 + (k + 1) % m, m + 1]
+        X = coord[t]
+        if np.linalg.det(np.c_[X[1] - X[0], X[2] - X[0], X[3] - X[0]]) < 0:
+            t[2], t[3] = t[3], t[2]
+        lnods.append(t)
+    u = np.random.default_rng(90 + m).standard_normal(coord.shape)
+    return coord, np.array(lnods, dtype=np.int32), u
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_longest_rows_of_the_row_gather(precision):
+    """Rows of 32 entries, the most the row gather takes (five bits of row
+    position per walk step), run on it and match the oracle, in the assembly
+    and the cached-geometry step; a 33-entry row makes the default mode fall
+    back to atomics (still matching) and an explicit row-gather request fail."""
+    coord, lnods, u = _fan_mesh(30)
+    asm = nsi.Assembler(coord, lnods, precision=precision)
+    assert asm.max_row == 32 and asm.scatter == nsi.SCATTERS["gather"]
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = (x.double().cpu().numpy() for x in asm.assemble(ut))
+    A_static, _ = asm.static_part()
+    A2, rhs2 = (x.double().cpu().numpy() for x in asm.assemble_convective(ut, A_static))
+    rp, ci = (x.cpu().numpy() for x in asm.pattern())
+    asm.close()
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    orp, oci, oA, oG, orhs = oracle.assemble(coord, lnods, uo, None, RHO, MU, DT)
+    np.testing.assert_array_equal(ci, oci)
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], err
+    err2 = errors(rp, A2, oG, rhs2, oA, oG, orhs)
+    assert max(err2.values()) <= TOL[precision], err2
+    coord, lnods, u = _fan_mesh(31)
+    asm = nsi.Assembler(coord, lnods, precision=precision)
+    assert asm.max_row == 33 and asm.scatter == nsi.SCATTERS["atomic"]
+    A, G, rhs = (x.double().cpu().numpy() for x in asm.assemble(torch.as_tensor(u.T.copy())))
+    rp = asm.pattern()[0].cpu().numpy()
+    asm.close()
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    _, _, oA, oG, orhs = oracle.assemble(coord, lnods, uo, None, RHO, MU, DT)
+    err = errors(rp, A, G, rhs, oA, oG, orhs)
+    assert max(err.values()) <= TOL[precision], err
+    with pytest.raises(nsi.NsiError) as ex:
+        nsi.Assembler(coord, lnods, precision=precision, scatter="gather")
+    assert ex.value.status == nsi.NSI_ERR_UNSUPPORTED
 
 
 def _sliver_mesh():
