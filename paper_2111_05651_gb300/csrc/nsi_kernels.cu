@@ -611,7 +611,7 @@ __device__ __forceinline__ WalkNode<typename Prec<P>::T, typename AccSmem<P>::Sl
 }
 
 template <int P, bool DEBUG>
-__device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nsteps, int len, int kd,
+__device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nsteps, int len,
                                          const T4<typename Prec<P>::T>* __restrict__ nb0,
                                          const T2<typename Prec<P>::T>* __restrict__ nb1, AccSmem<P>& acc, int t,
                                          int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
@@ -886,7 +886,7 @@ __device__ __forceinline__ void gather_compute(const MeshView& m, const FieldVie
       const T4<T> di = nb0[kd];
       const T2<T> ei = nb1[kd];
       const V3<T> u2i{di.w + di.w, ei.x + ei.x, ei.y + ei.y};
-      walk_row<P, DEBUG>(walk + s0, s1 - s0, len, kd, nb0, nb1, acc, t, R, u2i, kc, kmu, detsum, m.err);
+      walk_row<P, DEBUG>(walk + s0, s1 - s0, len, nb0, nb1, acc, t, R, u2i, kc, kmu, detsum, m.err);
       // diagonal from the partition of unity (sum_b grad N_b = 0, exact):
       //   A(i,i) = lumped mass - sum_{j != i} A(i,j)   (convection + viscous parts)
       //   G(i,i) = 1/3 sum_{j != i} G(i,j)            (each element adds c_i to three
@@ -1108,7 +1108,7 @@ struct AccA<NSI_FP64> {
 // NODAL, the convection w . c_x into the window's accumulators.  Same window,
 // orientation and carried cofactor as walk_row.
 template <int P, bool NODAL, bool DEBUG>
-__device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int nsteps, int len, int kd,
+__device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int nsteps, int len,
                                           const T4<typename Prec<P>::T>* __restrict__ nb0,
                                           const T2<typename Prec<P>::T>* __restrict__ nb1, AccA<P>& acc, int t,
                                           int R, const V3<typename Prec<P>::T>& u2i, typename Prec<P>::T kc,
@@ -1236,7 +1236,7 @@ __device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f,
       const T4<T> di = nb0[kd];
       const T2<T> ei = nb1[kd];
       const V3<T> u2i{di.w + di.w, ei.x + ei.x, ei.y + ei.y};
-      walk_step<P, NODAL, DEBUG>(smem + lay.walk() + b.s0, b.s1 - b.s0, b.len, kd, nb0, nb1, acc, t, R, u2i, kc,
+      walk_step<P, NODAL, DEBUG>(smem + lay.walk() + b.s0, b.s1 - b.s0, b.len, nb0, nb1, acc, t, R, u2i, kc,
                                  detsum, m.err);
       if constexpr (!NODAL) {  // C(i,i) = -sum_{j != i} C(i,j)
         Acc<P> rsum;
