@@ -439,11 +439,12 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
     s.g = add2(s.g, gxy);
     s.r = add2(s.r, gz_a);
   }
-  // sums over the row's slots t, t + R, ... (len of them) except slot kd
-  // (r[0]: A, r[1..3]: G_x..G_z)
-  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>* r) const {
+  // sums over the row's slots t, t + R, ... (len of them), the diagonal's
+  // included: it is still zero here (zeroed with the others; the walk only
+  // ever adds zeros to it), so no test is needed (r[0]: A, r[1..3]: G_x..G_z)
+  __device__ __forceinline__ void row_sums(int t, int R, int len, Acc<NSI_MIXED_F32_ACC32>* r) const {
+#pragma unroll 4
     for (int q = 0, k = t; q < len; ++q, k += R) {
-      if (k == kd) continue;
       const float4 v = a[k];
       r[0].add(v.w); r[1].add(v.x); r[2].add(v.y); r[3].add(v.z);
     }
@@ -483,10 +484,10 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     two_sum2(s.hr, s.lr, gz_a);
   }
   // (compensated sums on the float2 lanes (G_x, G_y) and (G_z, A))
-  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>* r) const {
+  __device__ __forceinline__ void row_sums(int t, int R, int len, Acc<NSI_MIXED_F32_ACC64>* r) const {
     float2 hg = make_float2(0.f, 0.f), lg = hg, hr = hg, lr = hg;
+#pragma unroll 4
     for (int q = 0, k = t; q < len; ++q, k += R) {
-      if (k == kd) continue;
       const float4 h = hi[k], l = lo[k];
       two_sum2(hg, lg, make_float2(h.x, h.y));
       two_sum2(hr, lr, make_float2(h.z, h.w));
@@ -531,9 +532,9 @@ struct AccSmem<NSI_FP64> {
   static __device__ __forceinline__ void update1(Slot& s, double A, double gx, double gy, double gz) {
     s.x.x += A; s.x.y += gx; s.y.x += gy; s.y.y += gz;
   }
-  __device__ __forceinline__ void row_sums(int t, int R, int len, int kd, Acc<NSI_FP64>* r) const {
+  __device__ __forceinline__ void row_sums(int t, int R, int len, Acc<NSI_FP64>* r) const {
+#pragma unroll 4
     for (int q = 0, k = t; q < len; ++q, k += R) {
-      if (k == kd) continue;
       const T2<double> x = a0[k], y = a1[k];
       r[0].add(x.x); r[1].add(x.y); r[2].add(y.x); r[3].add(y.y);
     }
@@ -894,7 +895,7 @@ __device__ __forceinline__ void gather_compute(const MeshView& m, const FieldVie
       Acc<P> rsum[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) rsum[c].zero();
-      acc.row_sums(t, R, len, kd, rsum);
+      acc.row_sums(t, R, len, rsum);  // (the diagonal slot is still zero)
       Acc<P> dg[4];
       if constexpr (P == NSI_MIXED_F32_ACC64) {
         const float p = kmass * detsum.hi;  // kmass * (hi + lo), product error kept
@@ -1053,9 +1054,9 @@ struct AccA<NSI_MIXED_F32_ACC32> {
   __device__ __forceinline__ Slot load1(int k) const { return a[k].x; }
   __device__ __forceinline__ void store1(int k, Slot v) { a[k].x = v; }
   static __device__ __forceinline__ void add(Slot& s, float x) { s += x; }
-  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC32>& r) const {
-    for (int q = 0, k = t; q < len; ++q, k += R)
-      if (k != kd) r.add(a[k].x);
+  __device__ __forceinline__ void row_sum(int t, int R, int len, Acc<NSI_MIXED_F32_ACC32>& r) const {
+#pragma unroll 4
+    for (int q = 0, k = t; q < len; ++q, k += R) r.add(a[k].x);
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>& r) { a[k].x = r.v; }
 };
@@ -1076,13 +1077,13 @@ struct AccA<NSI_MIXED_F32_ACC64> {
     s.x = sum;
     s.y += e;
   }
-  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_MIXED_F32_ACC64>& r) const {
-    for (int q = 0, k = t; q < len; ++q, k += R)
-      if (k != kd) {
-        const float4 v = a[k];
-        r.add(v.x);
-        r.lo += v.y;
-      }
+  __device__ __forceinline__ void row_sum(int t, int R, int len, Acc<NSI_MIXED_F32_ACC64>& r) const {
+#pragma unroll 4
+    for (int q = 0, k = t; q < len; ++q, k += R) {
+      const float4 v = a[k];
+      r.add(v.x);
+      r.lo += v.y;
+    }
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>& r) {
     reinterpret_cast<float2*>(a + k)[0] = make_float2(r.hi, r.lo);
@@ -1097,9 +1098,9 @@ struct AccA<NSI_FP64> {
   __device__ __forceinline__ Slot load1(int k) const { return a[k].x; }
   __device__ __forceinline__ void store1(int k, Slot v) { a[k].x = v; }
   static __device__ __forceinline__ void add(Slot& s, double x) { s += x; }
-  __device__ __forceinline__ void row_sum(int t, int R, int len, int kd, Acc<NSI_FP64>& r) const {
-    for (int q = 0, k = t; q < len; ++q, k += R)
-      if (k != kd) r.add(a[k].x);
+  __device__ __forceinline__ void row_sum(int t, int R, int len, Acc<NSI_FP64>& r) const {
+#pragma unroll 4
+    for (int q = 0, k = t; q < len; ++q, k += R) r.add(a[k].x);
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_FP64>& r) { a[k].x = r.v; }
 };
@@ -1241,7 +1242,7 @@ __device__ __forceinline__ void step_rows(const MeshView& m, const FieldView& f,
       if constexpr (!NODAL) {  // C(i,i) = -sum_{j != i} C(i,j)
         Acc<P> rsum;
         rsum.zero();
-        acc.row_sum(t, R, b.len, kd, rsum);
+        acc.row_sum(t, R, b.len, rsum);  // (the diagonal slot is still zero)
         Acc<P> dg;
         if constexpr (P == NSI_MIXED_F32_ACC64) {
           dg.hi = -rsum.hi;
