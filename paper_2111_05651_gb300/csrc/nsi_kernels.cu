@@ -683,7 +683,16 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
       detsum.add(f * det);
     }
     // the newest node always enters q; p keeps the older node or takes q's
-    if (w & WALK_EVQ) {
+    // (mixed32, whose nodes are smaller, measured up to 2% faster with
+    // selects; mixed64 3% slower, so the others keep the branch)
+    if constexpr (P == NSI_MIXED_F32_ACC32) {
+      const bool evq = (w & WALK_EVQ) != 0u;
+      const Node lv = evq ? q : p;
+      acc.store1(lv.k, lv.v);
+      p = evq ? p : q;
+      m = evq ? cq : cp;
+      sg = evq ? T(1) : T(-1);
+    } else if (w & WALK_EVQ) {
       acc.store1(q.k, q.v);
       m = cq;
       sg = T(1);
@@ -1138,7 +1147,6 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
     }
     return nd;
   };
-  const int last = nsteps - 1;
   // as walk_row: the two filling steps' nodes loaded directly
   Node p = load((int)(st[0] & WALK_POS) * R + t);
   Node q = load((int)(st[1] & WALK_POS) * R + t);
@@ -1148,7 +1156,7 @@ __device__ __forceinline__ void walk_step(const uint8_t* __restrict__ st, int ns
   Node c = load((int)(w & WALK_POS) * R + t);
 #pragma unroll 2
   for (int s = 2; s < nsteps; ++s) {
-    const unsigned wn = st[min(s + 1, last)];
+    const unsigned wn = st[min(s + 1, nsteps - 1)];
     const Node cn = load((int)(wn & WALK_POS) * R + t);
     const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);
     const bool elem = (w & WALK_ELEM) != 0u;
