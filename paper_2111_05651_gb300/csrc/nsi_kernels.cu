@@ -15,6 +15,7 @@
 //   fan_kernel      one CSR entry per thread, walking the ring of elements
 //                   around its edge (autotuning candidate)
 //   batched_kernel  the row gather over many meshes in one persistent launch
+//                   (their node records packed by one batched_pack_kernel)
 //   step_kernel     one time step with cached geometry (A_static + C(u),
 //                   rhs), or the paper's per-node outputs
 //   vjp_kernel      adjoint of R(u, mu) = A(u) u - b, element per thread
@@ -202,9 +203,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //          the float low parts (coordinates kept to ~2^-32 relative)
 //   FP64:  {x, y, z, 0} {ux, uy, uz, 0} as doubles
 template <int P>
-__global__ void __launch_bounds__(256) pack_kernel(MeshView m, FieldView f, void* __restrict__ rec) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= m.n) return;
+__device__ __forceinline__ void pack_node(const MeshView& m, const FieldView& f, void* __restrict__ rec, int64_t i) {
   if constexpr (P == NSI_FP64) {
     const D4 x = m.xyz64[i];
     const V3<double> u = load_vec<double>(f.u, i);
@@ -221,6 +220,12 @@ __global__ void __launch_bounds__(256) pack_kernel(MeshView m, FieldView f, void
                       (__float_as_uint(lo.x) >> 16) | (__float_as_uint(lo.y) & 0xffff0000u),
                       __float_as_uint(lo.z) & 0xffff0000u);
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) pack_kernel(MeshView m, FieldView f, void* __restrict__ rec) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m.n) pack_node<P>(m, f, rec, i);
 }
 
 __device__ __forceinline__ V3<float> record_lo(float w6, float w7) {
@@ -1743,6 +1748,15 @@ __device__ __forceinline__ const BatchItem& batch_item(const BatchArgs& args, in
   return args.item[lo];
 }
 
+// the node records of every mesh of a batch in one launch: block b packs the
+// nodes of the batch's row block b (the row gather's blocks of R rows)
+template <int P>
+__global__ void __launch_bounds__(128) batched_pack_kernel(const __grid_constant__ BatchArgs args) {
+  const BatchItem& it = batch_item(args, blockIdx.x);
+  const int64_t i = (blockIdx.x - it.block0) * (int64_t)blockDim.x + threadIdx.x;
+  if (i < it.m.n) pack_node<P>(it.m, it.f, const_cast<void*>(it.m.rec), i);
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) batched_kernel(const __grid_constant__ BatchArgs args, GatherSmem lay) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2236,9 +2250,10 @@ static nsi_status batched_core_p(NsiHandle* const* hs, const NsiFields* fs, cons
   }
   args.total_blocks = blocks;
   if (blocks == 0) return NSI_OK;
-  for (int k = 0; k < count; ++k)
-    pack_kernel<P><<<(hs[k]->n + 255) / 256, 256, 0, s>>>(args.item[k].m, args.item[k].f, hs[k]->rec);
-  nsi_status st = set_gather_smem<P, false>();
+  batched_pack_kernel<P><<<blocks, R, 0, s>>>(args);
+  nsi_status st = check_launch("batched_pack_kernel");
+  if (st) return st;
+  st = set_gather_smem<P, false>();
   if (st) return st;
   const GatherSmem lay = gather_smem(P, R, max_row, max_entries, max_steps);
   const size_t smem = lay.total();

@@ -240,9 +240,10 @@ def test_debug_checks_clean():
             assert max(err.values()) <= TOL[precision]
 
 
-def test_batched_equals_single():
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_batched_equals_single(precision):
     meshes = [meshgen.config_mesh(N=n, jitter=0.15, numbering="natural", seed=50 + n) for n in (3, 7, 5)]
-    asms = [nsi.Assembler(m.coord, m.lnods, precision="mixed64") for m, _ in meshes]
+    asms = [nsi.Assembler(m.coord, m.lnods, precision=precision) for m, _ in meshes]
     us = [torch.as_tensor(u.T.copy()) for _, u in meshes]
     singles = [[t.clone() for t in a.assemble(u)] for a, u in zip(asms, us)]
     batched = nsi.assemble_batched(asms, us)
