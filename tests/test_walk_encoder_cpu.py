@@ -52,7 +52,29 @@ def _write(path, mesh, u):
         np.ascontiguousarray(u, dtype=np.float64).tofile(f)
 
 
+def _small(coord, lnods, seed):
+    coord = np.asarray(coord, dtype=np.float64)
+    lnods = np.asarray(lnods, dtype=np.int32)
+    for e in range(len(lnods)):  # positive orientation
+        X = coord[lnods[e]]
+        if np.linalg.det(np.c_[X[1] - X[0], X[2] - X[0], X[3] - X[0]]) < 0:
+            lnods[e, [2, 3]] = lnods[e, [3, 2]]
+    return meshgen.Mesh(coord=coord, lnods=lnods), np.random.default_rng(seed).standard_normal(coord.shape)
+
+
+def _fan(m):
+    ang = 2 * np.pi * np.arange(m) / m
+    coord = np.vstack([[0, 0, 0], np.c_[np.cos(ang), np.sin(ang), np.zeros(m)], [0, 0, 1]])
+    return _small(coord, [[0, 1 + k, 1 + (k + 1) % m, m + 1] for k in range(m)], 70 + m)
+
+
 CASES = [
+    # every row of one tet walks 1 element; two tets on a face; a ring of 30
+    # tets around an edge (rows of 32 entries, the walk's limit)
+    ("one_tet", lambda: _small([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 1, 2, 3]], 71)),
+    ("two_tets", lambda: _small([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]],
+                                [[0, 1, 2, 3], [1, 2, 3, 4]], 72)),
+    ("fan30", lambda: _fan(30)),
     ("kuhn6_natural", lambda: meshgen.config_mesh(N=6, jitter=0.0, numbering="natural", seed=0)),
     ("kuhn9_random", lambda: meshgen.config_mesh(N=9, jitter=0.15, numbering="random", seed=1)),
     ("kuhn8_rcm", lambda: meshgen.config_mesh(N=8, jitter=0.15, numbering="rcm", seed=2)),
@@ -72,8 +94,9 @@ def test_walk_replays_the_star(replay, tmp_path, name, make):
     assert int(stats["elements"]) == 4 * mesh.n_elems
     assert int(stats["skipped"]) == 0 and int(stats["stale_reads"]) == 0
     assert float(stats["worst"]) <= 1e-12
-    # one path per row on the Kuhn cubes: two filling steps per row, then one per element
-    if name.startswith("kuhn"):
+    # one path per row on the Kuhn cubes and the small meshes: two filling
+    # steps per row, then one per element
+    if not name.startswith("delaunay"):
         assert int(stats["multipath_rows"]) == 0
         assert int(stats["steps"]) == int(stats["elements"]) + 2 * mesh.n_nodes
     else:
