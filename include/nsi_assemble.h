@@ -47,9 +47,11 @@
  *      NSI_MIXED_F32_ACC32 u, u_n: float;   A, G, rhs: float.
  *  - Outputs are OVERWRITTEN by every assemble call (the call defines every
  *    entry; no prior zeroing is needed).
- *  - nsi_assemble* never allocate device memory, never synchronise the
- *    stream, and only enqueue work on the given stream; they may be captured
- *    into a CUDA graph.  Errors detected on the device (only when the handle
+ *  - The device entry points (nsi_assemble, _mode, _batched, _convective,
+ *    _nodal, _vjp, nsi_residual) never allocate device memory, never
+ *    synchronise the stream, and only enqueue work on the given stream; they
+ *    may be captured into a CUDA graph.  nsi_assemble_host, for host buffers,
+ *    is the exception (see its comment).  Errors detected on the device (only when the handle
  *    was created with debug_checks) are reported by nsi_device_status().
  *  - Every function returns an nsi_status; on failure nsi_last_error()
  *    returns a human-readable message for the calling thread.  No C++
