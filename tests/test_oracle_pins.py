@@ -332,6 +332,25 @@ def test_rows_match_full_assembly():
         np.testing.assert_array_equal(rh, rhs[:, r])
 
 
+@pytest.mark.parametrize("rho,mu,dt", [(1.0, 1e-3, 1e-2), (2.5, 0.3, 0.05)])
+def test_residual_vanishes_for_constant_velocity(rho, mu, dt):
+    """R = A(u) u - b is zero for a constant velocity c with u^n = u: the
+    convection and viscous parts annihilate constants (the shape gradients of
+    an element sum to zero) and the lumped mass on the diagonal of A is the
+    same lumped mass that forms b.  Pins oracle.residual and the mass terms
+    together."""
+    mesh, _ = _mesh(5, 0.15, "random", seed=12)
+    c = np.array([0.7, -1.3, 2.1])
+    u = np.tile(c, (mesh.n_nodes, 1))
+    rp, ci, A, G, rhs = oracle.assemble(mesh.coord, mesh.lnods, u, None, rho, mu, dt)
+    R = oracle.residual((rp, ci, A), rhs, u)
+    assert np.abs(R).max() <= 1e-12 * np.abs(rhs).max()
+    # and a non-constant field does not give zero
+    u2 = u + 0.1 * mesh.coord
+    rp, ci, A2, G2, rhs2 = oracle.assemble(mesh.coord, mesh.lnods, u2, None, rho, mu, dt)
+    assert np.abs(oracle.residual((rp, ci, A2), rhs2, u2)).max() > 1e-6 * np.abs(rhs2).max()
+
+
 # ----------------------------------------------------------------------------
 # adjoint
 # ----------------------------------------------------------------------------
