@@ -264,7 +264,11 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOut
  * counterpart; this is an interface of this library only.)
  *
  * Same result as nsi_assemble in the row-gather mode, for a handle created
- * beforehand.  The call allocates nothing: the per-call node records go to a
+ * beforehand: the call runs the kernels nsi_assemble would run for the handle
+ * (the star or edge-fan row gather chosen by nsi_set_launch or the autotuner,
+ * the persistent grid, the bounds checks of a debug handle) and then, in the
+ * mixed precisions, the double-precision rows of badly shaped elements.  The
+ * call allocates nothing: the per-call node records go to a
  * scratch array compiled into the library (16 MiB, held by every GPU that
  * loads the library until the process exits), so meshes of at most 524,288
  * nodes in the mixed precisions and 262,144 nodes in FP64 are accepted;

@@ -66,6 +66,8 @@ def _load():
             lib.oracle_vjp.restype = ctypes.c_int
             lib.oracle_vjp.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _d, _d, _d]
+            lib.oracle_vjp_mu_abs.restype = ctypes.c_int
+            lib.oracle_vjp_mu_abs.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, _d, _d]
             _lib = lib
     return _lib
 
@@ -176,6 +178,19 @@ def vjp(coord, lnods, u, w, rho=1.0, mu=1e-3, dt=1e-2):
     if rc != 0:
         raise ValueError(f"oracle_vjp failed ({rc})")
     return gu, float(gmu[0])
+
+
+def vjp_mu_abs(coord, lnods, u, w, rho=1.0, mu=1e-3, dt=1e-2):
+    """Sum of the magnitudes of the terms of grad_mu (the scale of its rounding
+    error bound); see ``oracle_vjp_mu_abs``.  rho, mu and dt do not enter."""
+    lib = _load()
+    coord, lnods, u, w = _f64(coord), _ln(lnods), _f64(u), _f64(w)
+    out = np.zeros(1)
+    rc = lib.oracle_vjp_mu_abs(coord.shape[0], lnods.shape[0], _p(coord, _d), _p(lnods, _i32), _p(u, _d),
+                               _p(w, _d), _p(out, _d))
+    if rc != 0:
+        raise ValueError(f"oracle_vjp_mu_abs failed ({rc})")
+    return float(out[0])
 
 
 def residual(csr_A, rhs, u):

@@ -465,3 +465,49 @@ int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, 
     *grad_mu = gmu;
     return 0;
 }
+
+/*
+ * Condition scale of grad_mu: the sum, over elements e, Gauss points g and
+ * node/component pairs (a, k), of the magnitudes of the terms whose sum is
+ * grad_mu in oracle_vjp,
+ *   sum |w[a][k] gpvol_g (gpcar_a . grad u^k)|.
+ * A floating-point evaluation of grad_mu in any summation order differs from
+ * the exact sum by at most (number of terms) x (rounding unit) x this scale
+ * (the standard error bound of a floating-point sum), so comparisons of the
+ * cancelling scalar grad_mu are made relative to it.
+ */
+int oracle_vjp_mu_abs(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
+                      const double* w, double* out) {
+    double shape[PGAUS][PNODE], weight[PGAUS];
+    gauss_rule(shape, weight);
+    double s = 0.0;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        for (int a = 0; a < PNODE; ++a)
+            if (ln[a] < 0 || ln[a] >= n) return -1;
+        double X[PNODE][NDIME], U[PNODE][NDIME], W[PNODE][NDIME];
+        for (int a = 0; a < PNODE; ++a)
+            for (int k = 0; k < NDIME; ++k) {
+                X[a][k] = coord[3 * (int64_t)ln[a] + k];
+                U[a][k] = u[3 * (int64_t)ln[a] + k];
+                W[a][k] = w[3 * (int64_t)ln[a] + k];
+            }
+        double gpcar[PNODE][NDIME];
+        const double det = cartesian_derivatives(X, gpcar);
+        double gradu[NDIME][NDIME];
+        for (int k = 0; k < NDIME; ++k)
+            for (int l = 0; l < NDIME; ++l) {
+                gradu[k][l] = 0.0;
+                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * gpcar[c][l];
+            }
+        for (int g = 0; g < PGAUS; ++g)
+            for (int a = 0; a < PNODE; ++a)
+                for (int k = 0; k < NDIME; ++k) {
+                    double dmu = 0.0;
+                    for (int i = 0; i < NDIME; ++i) dmu += gpcar[a][i] * gradu[k][i];
+                    s += fabs(W[a][k] * weight[g] * det * dmu);
+                }
+    }
+    *out = s;
+    return 0;
+}

@@ -2051,9 +2051,13 @@ static nsi_status fix_exact_rows(NsiHandle* h, const FieldView& f, int mode, voi
   }
 }
 
+// `rec` (nullptr: the handle's buffer) receives the row gather's per-call
+// node records
 template <int P>
-static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s) {
-  const MeshView m = view_of(h);
+static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s,
+                                  void* rec = nullptr) {
+  MeshView m = view_of(h);
+  if (rec) m.rec = rec;
   const int blk = 256;
   if (mode == NSI_SCATTER_ATOMIC) {
     nsi_status st = zero_outputs<P>(h, o, s);
@@ -2086,7 +2090,7 @@ static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutVie
   if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
   nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
   if (st) return st;
-  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, h->rec);
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
   if (h->use_fan) {
     const size_t fsm = FanSmem<P>::total(FAN_BLOCK);
     if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
@@ -2388,23 +2392,14 @@ static nsi_status noalloc_scratch(int dev, void** out) {
   return NSI_OK;
 }
 
+// the row gather of nsi_assemble (the same kernels and launch choice: star or
+// edge-fan kernel, persistent grid, debug checks) with the node records in
+// the static scratch, then the double-precision rows of badly shaped elements
 template <int P>
 static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const OutView& o, void* scratch,
                                      cudaStream_t s) {
-  nsi_status st = set_gather_smem<P, false>();
+  nsi_status st = assemble_core_p<P>(h, f, o, NSI_SCATTER_GATHER, s, scratch);
   if (st) return st;
-  MeshView m = view_of(h);
-  m.rec = scratch;
-  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, scratch);
-  if (h->use_fan) {
-    fan_kernel<P, false><<<h->fan_blocks, FAN_BLOCK, FanSmem<P>::total(FAN_BLOCK), s>>>(m, f, o);
-    return check_launch("fan_kernel (no-alloc)");
-  }
-  const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
-  gather_kernel<P, false><<<h->plan.n_blocks, R, lay.total(), s>>>(m, f, o, lay, 0);
-  nsi_status st2 = check_launch("gather_kernel (no-alloc)");
-  if (st2) return st2;
   return fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
 }
 

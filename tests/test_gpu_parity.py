@@ -307,7 +307,7 @@ def test_residual_matches_oracle(precision):
     Ro = oracle.residual((rp, ci, oA), orhs, uo)   # [n, 3]
     tol = 1e-12 if precision == "fp64" else 1e-5
     scale = np.abs(Ro).max()
-    assert np.abs(R.T - Ro).max() <= tol * scale * 10
+    assert np.abs(R.T - Ro).max() <= tol * scale
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64"])
@@ -322,7 +322,11 @@ def test_vjp_matches_oracle(precision):
     tol = 1e-12 if precision == "fp64" else 1e-5
     gu = gu.double().cpu().numpy().T
     assert np.abs(gu - ogu).max() <= tol * np.abs(ogu).max()
-    assert abs(float(gmu.item()) - ogmu) <= tol * max(abs(ogmu), 1e-30) * 10
+    # grad_mu is one sum of terms of both signs over every element: its error
+    # is bounded by the rounding unit times the sum of the terms' magnitudes
+    # (the standard bound for a floating-point sum), so that sum is the scale
+    gabs = oracle.vjp_mu_abs(mesh.coord, mesh.lnods, uo, wo, RHO, MU, DT)
+    assert abs(float(gmu.item()) - ogmu) <= tol * gabs
 
 
 def test_autograd_residual():

@@ -425,3 +425,34 @@ def test_vjp_closed_form():
         ref_mu += vol * np.sum(Wn * (grad @ gradu.T))
     np.testing.assert_allclose(gu, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     assert gmu == pytest.approx(ref_mu, rel=1e-12)
+
+
+def test_vjp_mu_abs_brute_force():
+    """The grad_mu error scale: the sum over elements, the 4 Gauss points and
+    (a, k) of |w_ak (|T|/4) grad N_a . grad u^k|, with the gradients from the
+    independent 4x4 inversion; and |grad_mu| never exceeds it, with equality
+    when no term is negative (one tet, u = x, w the signs of the gradients)."""
+    mesh, u = meshgen.config_mesh(N=2, jitter=0.15, numbering="random", seed=71)
+    w = np.random.default_rng(72).standard_normal(u.shape)
+    s = 0.0
+    for ln in mesh.lnods:
+        X = mesh.coord[ln]
+        M = np.hstack([np.ones((4, 1)), X])
+        grad = np.linalg.inv(M)[1:, :].T
+        vol = abs(np.linalg.det(M)) / 6.0
+        gradu = u[ln].T @ grad                     # gradu[k] = grad u^k
+        terms = w[ln] * (grad @ gradu.T) * vol / 4  # [a, k], one Gauss point
+        s += 4 * np.abs(terms).sum()
+    got = oracle.vjp_mu_abs(mesh.coord, mesh.lnods, u, w)
+    assert got == pytest.approx(s, rel=RTOL)
+    _, gmu = oracle.vjp(mesh.coord, mesh.lnods, u, w, 1.0, 1e-3, 1e-2)
+    assert abs(gmu) <= got
+    # one tet, u linear with grad u^k = e_k and w_ak = grad N_a[k] sign-matched:
+    # every term w_ak grad N_a . e_k = w_ak dN_a/dx_k is |dN_a/dx_k| >= 0
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    ln1 = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    grad = np.linalg.inv(np.hstack([np.ones((4, 1)), X]))[1:, :].T
+    u1 = X.copy()
+    w1 = np.sign(grad)
+    _, gmu1 = oracle.vjp(X, ln1, u1, w1, 1.0, 1e-3, 1e-2)
+    assert gmu1 == pytest.approx(oracle.vjp_mu_abs(X, ln1, u1, w1), rel=RTOL)

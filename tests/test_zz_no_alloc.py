@@ -74,3 +74,45 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     msg = lib.nsi_last_error().decode()
     assert "274625 nodes" in msg and "scratch" in msg
     asm.close()
+
+
+def _sliver_mesh():
+    """4^3 Kuhn cube with node (2,2,2) moved by 0.499 h along (1,-1,0): two
+    slivers whose rows the mixed modes recompute in double after the kernel."""
+    mesh, u = meshgen.config_mesh(N=4, jitter=0.0, numbering="natural", seed=0)
+    coord = mesh.coord.copy()
+    coord[2 + 5 * (2 + 5 * 2)] += 0.499 * 0.25 * np.array([1.0, -1.0, 0.0])
+    return meshgen.Mesh(coord=coord, lnods=mesh.lnods, N=4), u
+
+
+@pytest.mark.parametrize("precision", ["mixed64", "mixed32"])
+@pytest.mark.parametrize("launch", ["fan", "star-debug"])
+def test_noalloc_same_kernels_and_fixup(precision, launch):
+    """The allocation-free call runs whatever nsi_assemble runs for the handle:
+    the edge-fan kernel when nsi_set_launch(-1) selected it, the bounds-checked
+    kernels of a debug handle, and in both cases the double-precision rows of
+    badly shaped elements afterwards."""
+    lib = nsi.load_library()
+    mesh, u = _sliver_mesh()
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter="gather",
+                        debug_checks=(launch == "star-debug"))
+    assert asm.info().exact_rows > 0
+    if launch == "fan":
+        nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
+        assert asm.info().rows_per_block == -1
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    u2 = meshgen.add_noise(u, 0.3, np.random.default_rng(64))
+    for uu in (u, u2):
+        ut = torch.as_tensor(uu.T.copy())
+        ref = [t.clone() for t in asm.assemble(ut)]
+        fields, keep = asm.fields(ut, None, 1.0, 1e-3, 1e-2)
+        outs = asm.empty_outputs()
+        for t in outs:
+            t.fill_(float("nan"))
+        status = _noalloc(lib, asm, fields, outs, stream)
+        torch.cuda.synchronize()
+        assert status == nsi.NSI_OK, lib.nsi_last_error().decode()
+        for got, want in zip(outs, ref):
+            assert torch.equal(got, want)
+    asm.device_status()  # raises if a device-side bounds check fired
+    asm.close()
