@@ -386,6 +386,20 @@ __device__ __forceinline__ double normalised_pair_double(float hi, float lo) {
 __device__ __forceinline__ double nonfinite_double(float hi) { return __longlong_as_double(f32_to_f64_bits(hi)); }
 // true if the exponent bits of x are all ones (infinite or NaN)
 __device__ __forceinline__ bool nonfinite_bits(float x) { return (__float_as_uint(x) | 0x807fffffu) == 0xffffffffu; }
+// true for an infinite, NaN or subnormal float (the cases float_double leaves out)
+__device__ __forceinline__ bool special_float(float x) {
+  const unsigned e = __float_as_uint(x) & 0x7f800000u;
+  return e == 0x7f800000u || (e == 0u && (__float_as_uint(x) & 0x007fffffu) != 0u);
+}
+// the double equal to a normal or zero float, from its bit pattern: the
+// exponent rebiased (+896), the 23 mantissa bits moved to the top of the
+// double's 52; the sign kept
+__device__ __forceinline__ double float_double(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned a = u & 0x7fffffffu;
+  const unsigned hi = (a == 0u ? 0u : (a >> 3) + (896u << 20)) | (u & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
 // the double nearest hi + lo of a pair with a finite hi: renormalised first
 // (Fast2Sum)
 __device__ __forceinline__ double pair_double(float hi, float lo) {
@@ -467,57 +481,66 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
     return {v.w, v.x, v.y, v.z};
   }
 };
+// mixed64: the A value as a compensated pair (leading part with G in one
+// float4, error term in its own array), the pressure-gradient sums in plain
+// float.  G's element terms -c_i / 24 are float products, and its sums over
+// the ~5 elements of an edge carry a few float roundings (about 1e-7 of the
+// row's largest entry); A, whose diagonal is the lumped mass minus the row's
+// other entries (the row sums of the convection and viscous terms cancel),
+// keeps the compensated sum (about 48 significant bits).
 template <>
 struct AccSmem<NSI_MIXED_F32_ACC64> {
-  float4* __restrict__ hi;
-  float4* __restrict__ lo;
+  float4* __restrict__ hi;  // (G_x, G_y, G_z, A leading part)
+  float* __restrict__ lo;   // A error term
   __device__ __forceinline__ AccSmem(unsigned char* p, size_t N)
-      : hi(reinterpret_cast<float4*>(p)), lo(reinterpret_cast<float4*>(p) + N) {}
+      : hi(reinterpret_cast<float4*>(p)), lo(reinterpret_cast<float*>(p) + 4 * N) {}
   __device__ __forceinline__ void zero(int k) {
     hi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    lo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    lo[k] = 0.f;
   }
   struct Slot {
-    float2 hg, hr, lg, lr;  // leading parts and error terms of (G_x, G_y) and (G_z, A)
+    float2 g, r;  // (G_x, G_y), (G_z, A leading part)
+    float l;      // A error term
   };
   __device__ __forceinline__ Slot load1(int k) const {
-    const float4 h = hi[k], l = lo[k];
-    return {make_float2(h.x, h.y), make_float2(h.z, h.w), make_float2(l.x, l.y), make_float2(l.z, l.w)};
+    const float4 h = hi[k];
+    return {make_float2(h.x, h.y), make_float2(h.z, h.w), lo[k]};
   }
   __device__ __forceinline__ void store1(int k, const Slot& v) {
-    hi[k] = make_float4(v.hg.x, v.hg.y, v.hr.x, v.hr.y);
-    lo[k] = make_float4(v.lg.x, v.lg.y, v.lr.x, v.lr.y);
+    hi[k] = make_float4(v.g.x, v.g.y, v.r.x, v.r.y);
+    lo[k] = v.l;
   }
+  // G plain, A by TwoSum on its lane of the (G_z, A) pair
   static __device__ __forceinline__ void add(Slot& s, float2 gxy, float2 gz_a) {
-    two_sum2(s.hg, s.lg, gxy);
-    two_sum2(s.hr, s.lr, gz_a);
+    s.g = add2(s.g, gxy);
+    const float2 t = add2(s.r, gz_a);
+    const float bb = t.y - s.r.y;
+    s.l += (s.r.y - (t.y - bb)) + (gz_a.y - bb);
+    s.r = t;
   }
-  // (compensated sums on the float2 lanes (G_x, G_y) and (G_z, A))
+  // sums over the row's slots, the diagonal's included (still zero): A
+  // compensated, G plain (r[0]: A, r[1..3]: G_x..G_z with zero error terms)
   __device__ __forceinline__ void row_sums(int t, int R, int len, Acc<NSI_MIXED_F32_ACC64>* r) const {
-    float2 hg = make_float2(0.f, 0.f), lg = hg, hr = hg, lr = hg;
+    float2 g = make_float2(0.f, 0.f), za = g;
+    float al = 0.f;
 #pragma unroll 4
     for (int q = 0, k = t; q < len; ++q, k += R) {
-      const float4 h = hi[k], l = lo[k];
-      two_sum2(hg, lg, make_float2(h.x, h.y));
-      two_sum2(hr, lr, make_float2(h.z, h.w));
-      lg = add2(lg, make_float2(l.x, l.y));
-      lr = add2(lr, make_float2(l.z, l.w));
+      const float4 h = hi[k];
+      g = add2(g, make_float2(h.x, h.y));
+      const float2 t2 = add2(za, make_float2(h.z, h.w));
+      const float bb = t2.y - za.y;
+      al += ((za.y - (t2.y - bb)) + (h.w - bb)) + lo[k];
+      za = t2;
     }
-    r[0].hi = hr.y; r[0].lo = lr.y;
-    r[1].hi = hg.x; r[1].lo = lg.x;
-    r[2].hi = hg.y; r[2].lo = lg.y;
-    r[3].hi = hr.x; r[3].lo = lr.x;
+    r[0].hi = za.y; r[0].lo = al;
+    r[1].hi = g.x; r[1].lo = 0.f;
+    r[2].hi = g.y; r[2].lo = 0.f;
+    r[3].hi = za.x; r[3].lo = 0.f;
   }
+  // the diagonal: A as a pair, G as the leading parts
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>* r) {
     hi[k] = make_float4(r[1].hi, r[2].hi, r[3].hi, r[0].hi);
-    lo[k] = make_float4(r[1].lo, r[2].lo, r[3].lo, r[0].lo);
-  }
-  // (leading, error) pairs of one half of slot k: half 0 gives G_x and G_y,
-  // half 1 gives G_z and A
-  __device__ __forceinline__ float4 pairs(int k, int half) const {
-    const float2 h = reinterpret_cast<const float2*>(hi)[2 * k + half];
-    const float2 l = reinterpret_cast<const float2*>(lo)[2 * k + half];
-    return make_float4(h.x, l.x, h.y, l.y);
+    lo[k] = r[0].lo;
   }
 };
 template <>
@@ -922,10 +945,9 @@ __device__ __forceinline__ void gather_compute(const MeshView& m, const FieldVie
         dg[0].add(-rsum[0].hi);
         dg[0].lo -= rsum[0].lo;
 #pragma unroll
-        for (int c = 1; c < 4; ++c) {
-          const float q = rsum[c].hi * (1.0f / 3.0f);
-          dg[c].hi = q;
-          dg[c].lo = fmaf(rsum[c].hi, 1.0f / 3.0f, -q) + rsum[c].lo * (1.0f / 3.0f);
+        for (int c = 1; c < 4; ++c) {  // G: plain float
+          dg[c].hi = rsum[c].hi * (1.0f / 3.0f);
+          dg[c].lo = 0.f;
         }
       } else {
         dg[0].v = kmass * detsum.v - rsum[0].v;
@@ -990,44 +1012,60 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
       dst[3][k] = stage[3 * L + k];
     }
   } else {
-    // double values out of compensated float slots, two components per
-    // staging round: every thread stages its own row's (leading, error) pairs
-    // in CSR order, then the block converts them while streaming them out
-    // coalesced (the conversions spread evenly over the threads)
+    // mixed64: two staging rounds, A (a (leading, error) pair, renormalised
+    // and converted to the nearest double in the coalesced loop) with G_x,
+    // then G_y and G_z (floats, converted exactly).  Every thread stages its
+    // own row's values in CSR order; the block then converts and streams them
+    // out coalesced (the conversions spread evenly over the threads).
     float2* pairs = reinterpret_cast<float2*>(smem + lay.nb0());
-    bool nonfinite = false;  // an infinite or NaN value among the thread's (rare; fixed after the loop)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      if (t < nrows) {
+    float* fl = reinterpret_cast<float*>(smem + lay.nb0());
+    // an infinite, NaN or subnormal value among the thread's (rare): such
+    // values are rewritten after the coalesced loop
+    bool special = false;
+    if (t < nrows) {
 #pragma unroll 4
-        for (int q = 0; q < len; ++q) {
-          const float4 pr = acc.pairs(q * R + t, half);
-          pairs[lb + q] = make_float2(pr.x, pr.y);
-          pairs[L + lb + q] = make_float2(pr.z, pr.w);
-          nonfinite |= nonfinite_bits(pr.x) | nonfinite_bits(pr.z);
-        }
+      for (int q = 0, k = t; q < len; ++q, k += R) {
+        const float4 h = acc.hi[k];
+        pairs[lb + q] = make_float2(h.w, acc.lo[k]);
+        fl[2 * L + lb + q] = h.x;
+        special |= nonfinite_bits(h.w) | special_float(h.x);
       }
-      const bool fix = __syncthreads_or(nonfinite);
-      // half 0: G_x, G_y; half 1: G_z, A
-      Out* d0 = half ? dst[3] : dst[1];
-      Out* d1 = half ? dst[0] : dst[2];
+    }
+    bool fix = __syncthreads_or(special);
+    for (int k = t; k < L; k += R) {
+      const float2 a = pairs[k];
+      const float sh = a.x + a.y;  // Fast2Sum: |error| <= ulp(leading) / 2
+      const float sl = a.y - (sh - a.x);
+      dst[0][k] = normalised_pair_double(sh, sl);
+      dst[1][k] = float_double(fl[2 * L + k]);
+    }
+    if (fix) {  // block-uniform: infinite and NaN values keep their class, subnormal floats are exact
       for (int k = t; k < L; k += R) {
-        const float2 a = pairs[k], b = pairs[L + k];
-        // both pairs renormalised at once (Fast2Sum on the float2 lanes, so
-        // that |error| <= ulp(leading) / 2), then converted
-        const float2 h = make_float2(a.x, b.x), l = make_float2(a.y, b.y);
-        const float2 sh = add2(h, l);
-        const float2 sl = sub2(l, sub2(sh, h));
-        d0[k] = normalised_pair_double(sh.x, sl.x);
-        d1[k] = normalised_pair_double(sh.y, sl.y);
+        if (nonfinite_bits(pairs[k].x)) dst[0][k] = nonfinite_double(pairs[k].x);
+        if (special_float(fl[2 * L + k])) dst[1][k] = __longlong_as_double(f32_to_f64_bits(fl[2 * L + k]));
       }
-      if (fix) {  // block-uniform: infinite and NaN values keep their class
-        for (int k = t; k < L; k += R) {
-          if (nonfinite_bits(pairs[k].x)) d0[k] = nonfinite_double(pairs[k].x);
-          if (nonfinite_bits(pairs[L + k].x)) d1[k] = nonfinite_double(pairs[L + k].x);
-        }
+    }
+    __syncthreads();
+    special = false;
+    if (t < nrows) {
+#pragma unroll 4
+      for (int q = 0, k = t; q < len; ++q, k += R) {
+        const float4 h = acc.hi[k];
+        fl[lb + q] = h.y;
+        fl[L + lb + q] = h.z;
+        special |= special_float(h.y) | special_float(h.z);
       }
-      if (half == 0) __syncthreads();
+    }
+    fix = __syncthreads_or(special);
+    for (int k = t; k < L; k += R) {
+      dst[2][k] = float_double(fl[k]);
+      dst[3][k] = float_double(fl[L + k]);
+    }
+    if (fix) {
+      for (int k = t; k < L; k += R) {
+        if (special_float(fl[k])) dst[2][k] = __longlong_as_double(f32_to_f64_bits(fl[k]));
+        if (special_float(fl[L + k])) dst[3][k] = __longlong_as_double(f32_to_f64_bits(fl[L + k]));
+      }
     }
   }
 }
