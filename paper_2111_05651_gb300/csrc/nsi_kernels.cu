@@ -393,12 +393,38 @@ __device__ __forceinline__ bool special_float(float x) {
 }
 // the double equal to a normal or zero float, from its bit pattern: the
 // exponent rebiased (+896), the 23 mantissa bits moved to the top of the
-// double's 52; the sign kept
+// double's 52; the sign kept.  A subnormal float (below 2^-126 in magnitude)
+// gives a signed zero; infinite and NaN floats are not handled (the values
+// converted this way are the pressure-gradient sums, functions of the
+// coordinates a handle validates, far inside the float range for any mesh
+// whose float element arithmetic is meaningful).
 __device__ __forceinline__ double float_double(float x) {
   const unsigned u = __float_as_uint(x);
   const unsigned a = u & 0x7fffffffu;
-  const unsigned hi = (a == 0u ? 0u : (a >> 3) + (896u << 20)) | (u & 0x80000000u);
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned hi = (a < 0x00800000u ? 0u : (a >> 3) + (896u << 20)) | (u & 0x80000000u);
+  return __hiloint2double((int)hi, a < 0x00800000u ? 0 : (int)(u << 29));
+}
+// The double nearest hi + lo for a renormalised float pair (|lo| <= ulp(hi) /
+// 2), from the bit patterns: the double of |hi| plus lo, with hi's sign taken
+// out, counted in units of that double's last place, k = round(lo 2^(52-E))
+// for hi's exponent E (|k| <= 2^28; the float product is exact and the
+// conversion rounds to nearest even, as do the low 29 bits of |hi|'s double,
+// all zero); when |hi| is a power of two and lo points below it, the sum lies
+// in the binade below, whose units are half as large (k doubled); hi's sign
+// is set last.  Exact for hi = lo = 0 and for hi of exponent field 53..254;
+// `slow` is set for the rest (hi below 2^-74, infinite or NaN), which the
+// caller converts another way.
+__device__ __forceinline__ double pair_double_fast(float hi, float lo, bool& slow) {
+  const unsigned u = __float_as_uint(hi);
+  const unsigned a = u & 0x7fffffffu;
+  const unsigned eh = a >> 23;
+  slow |= (eh - 53u > 201u) & (a != 0u);
+  const float ls = __uint_as_float(__float_as_uint(lo) ^ (u & 0x80000000u));
+  const unsigned below = ((a & 0x007fffffu) == 0u && ls < 0.0f) ? 1u : 0u;
+  const int k = __float2int_rn(ls * __uint_as_float(((306u + below - eh) & 0xffu) << 23));
+  const unsigned long long mag = a == 0u ? 0ull : ((unsigned long long)a << 29) + (896ull << 52);
+  return __longlong_as_double((long long)((mag + (unsigned long long)(long long)k) |
+                                          ((unsigned long long)(u & 0x80000000u) << 32)));
 }
 // the double nearest hi + lo of a pair with a finite hi: renormalised first
 // (Fast2Sum)
@@ -666,18 +692,19 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
   // encoder begins the first path that way): their nodes are loaded directly,
   // with the cofactor the first element carries, c_c = d_p x d_q
   Node p = walk_load<P>((int)(st[0] & WALK_POS) * R + t, nb0, nb1, acc);
-  Node q = walk_load<P>((int)(st[1] & WALK_POS) * R + t, nb0, nb1, acc);
-  V3<T> m = cross(p.d, q.d);
+  Node n0 = walk_load<P>((int)(st[1] & WALK_POS) * R + t, nb0, nb1, acc);
+  V3<T> m = cross(p.d, n0.d);
   T sg = T(-1);  // c_c = -sg m
   unsigned w = st[2];
-  Node c = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
-#pragma unroll 2  // two steps' arithmetic interleave (measured faster)
-  for (int s = 2; s < nsteps; ++s) {
-    // the next step's node, in flight while this element is evaluated (never
-    // one of p, q, c: the walk is encoded that way; the last step reloads its
-    // own node, unused)
+  Node n1 = walk_load<P>((int)(w & WALK_POS) * R + t, nb0, nb1, acc);
+  Node n2;
+  // One step: the element (i, p, q, c); the next step's node is loaded into
+  // nx (in flight while the element is evaluated; never one of p, q, c: the
+  // walk is encoded that way; the last step reloads its own node, unused).
+  // Afterwards the window is (p, c): p keeps its node or takes q's.
+  auto step = [&](Node& q, Node& c, Node& nx, int s) {
     const unsigned wn = st[s + 1 < nsteps ? s + 1 : s];
-    const Node cn = walk_load<P>((int)(wn & WALK_POS) * R + t, nb0, nb1, acc);
+    nx = walk_load<P>((int)(wn & WALK_POS) * R + t, nb0, nb1, acc);
     const V3<T> cp = cross(q.d, c.d), cq = cross(c.d, p.d);
     const bool elem = (w & WALK_ELEM) != 0u;
     if constexpr (P == NSI_FP64) {
@@ -714,32 +741,35 @@ __device__ __forceinline__ void walk_row(const uint8_t* __restrict__ st, int nst
       AccSmem<P>::add(c.v, gxy, __fmul2_rn(make_float2(ci.z, dot(w3, m)), make_float2(fg, -f * sg)));
       detsum.add(f * det);
     }
-    // the newest node always enters q; p keeps the older node or takes q's
-    // (mixed32, whose nodes are smaller, measured up to 2% faster with
-    // selects; mixed64 3% slower, so the others keep the branch)
-    if constexpr (P == NSI_MIXED_F32_ACC32) {
-      const bool evq = (w & WALK_EVQ) != 0u;
-      const Node lv = evq ? q : p;
-      acc.store1(lv.k, lv.v);
-      p = evq ? p : q;
-      m = evq ? cq : cp;
-      sg = evq ? T(1) : T(-1);
-    } else if (w & WALK_EVQ) {
-      acc.store1(q.k, q.v);
-      m = cq;
-      sg = T(1);
-    } else {
-      acc.store1(p.k, p.v);
-      p = q;
-      m = cp;
-      sg = T(-1);
-    }
-    q = c;
-    c = cn;
+    const bool evq = (w & WALK_EVQ) != 0u;
+    const Node& lv = evq ? q : p;  // the node that leaves the window
+    acc.store1(lv.k, lv.v);
+    if (!evq) p = q;
+    m = evq ? cq : cp;
+    sg = evq ? T(1) : T(-1);
     w = wn;
+  };
+  // The nodes q, c and the one in flight rotate through n0, n1, n2: three
+  // steps per iteration bring them back to their places, so the newest node
+  // never moves between registers (only p's update depends on the walk).
+  int s = 2;
+  for (; s + 3 <= nsteps; s += 3) {
+    step(n0, n1, n2, s);
+    step(n1, n2, n0, s + 1);
+    step(n2, n0, n1, s + 2);
+  }
+  if (s < nsteps) {
+    step(n0, n1, n2, s);
+    if (s + 1 < nsteps) {
+      step(n1, n2, n0, s + 1);
+      acc.store1(n2.k, n2.v);
+    } else {
+      acc.store1(n1.k, n1.v);
+    }
+  } else {
+    acc.store1(n0.k, n0.v);
   }
   acc.store1(p.k, p.v);
-  acc.store1(q.k, q.v);
 }
 
 // Per-thread view of one block of rows [r0, r0 + blockDim.x) of one mesh.
@@ -1012,59 +1042,46 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
       dst[3][k] = stage[3 * L + k];
     }
   } else {
-    // mixed64: two staging rounds, A (a (leading, error) pair, renormalised
-    // and converted to the nearest double in the coalesced loop) with G_x,
-    // then G_y and G_z (floats, converted exactly).  Every thread stages its
-    // own row's values in CSR order; the block then converts and streams them
-    // out coalesced (the conversions spread evenly over the threads).
-    float2* pairs = reinterpret_cast<float2*>(smem + lay.nb0());
-    float* fl = reinterpret_cast<float*>(smem + lay.nb0());
-    // an infinite, NaN or subnormal value among the thread's (rare): such
-    // values are rewritten after the coalesced loop
-    bool special = false;
+    // mixed64: one staging round.  Every thread stages its own row's values
+    // in CSR order -- A as its (leading, error) pair and the three G floats,
+    // G_z in the half of nb1 that the next block's column indices (copied in
+    // under this write-out by the persistent grid) leave free -- then the
+    // block converts them to double and streams them out coalesced (the
+    // conversions spread evenly over the threads).  A pair whose leading part
+    // is infinite, NaN or below 2^-74 is converted again by a rare pass.
+    float2* pa = reinterpret_cast<float2*>(smem + lay.nb0());
+    float* gx = reinterpret_cast<float*>(smem + lay.nb0()) + 2 * L;
+    float* gy = gx + L;
+    float* gz = reinterpret_cast<float*>(smem + lay.nb1()) + lay.N();
     if (t < nrows) {
 #pragma unroll 4
       for (int q = 0, k = t; q < len; ++q, k += R) {
         const float4 h = acc.hi[k];
-        pairs[lb + q] = make_float2(h.w, acc.lo[k]);
-        fl[2 * L + lb + q] = h.x;
-        special |= nonfinite_bits(h.w) | special_float(h.x);
-      }
-    }
-    bool fix = __syncthreads_or(special);
-    for (int k = t; k < L; k += R) {
-      const float2 a = pairs[k];
-      const float sh = a.x + a.y;  // Fast2Sum: |error| <= ulp(leading) / 2
-      const float sl = a.y - (sh - a.x);
-      dst[0][k] = normalised_pair_double(sh, sl);
-      dst[1][k] = float_double(fl[2 * L + k]);
-    }
-    if (fix) {  // block-uniform: infinite and NaN values keep their class, subnormal floats are exact
-      for (int k = t; k < L; k += R) {
-        if (nonfinite_bits(pairs[k].x)) dst[0][k] = nonfinite_double(pairs[k].x);
-        if (special_float(fl[2 * L + k])) dst[1][k] = __longlong_as_double(f32_to_f64_bits(fl[2 * L + k]));
+        pa[lb + q] = make_float2(h.w, acc.lo[k]);
+        gx[lb + q] = h.x;
+        gy[lb + q] = h.y;
+        gz[lb + q] = h.z;
       }
     }
     __syncthreads();
-    special = false;
-    if (t < nrows) {
-#pragma unroll 4
-      for (int q = 0, k = t; q < len; ++q, k += R) {
-        const float4 h = acc.hi[k];
-        fl[lb + q] = h.y;
-        fl[L + lb + q] = h.z;
-        special |= special_float(h.y) | special_float(h.z);
-      }
-    }
-    fix = __syncthreads_or(special);
+    bool slow = false;
     for (int k = t; k < L; k += R) {
-      dst[2][k] = float_double(fl[k]);
-      dst[3][k] = float_double(fl[L + k]);
+      const float2 a = pa[k];
+      const float sh = a.x + a.y;  // Fast2Sum: |error| <= ulp(leading) / 2
+      const float sl = a.y - (sh - a.x);
+      dst[0][k] = pair_double_fast(sh, sl, slow);
+      dst[1][k] = float_double(gx[k]);
+      dst[2][k] = float_double(gy[k]);
+      dst[3][k] = float_double(gz[k]);
     }
-    if (fix) {
+    if (__syncthreads_or(slow)) {  // block-uniform and rare
       for (int k = t; k < L; k += R) {
-        if (special_float(fl[k])) dst[2][k] = __longlong_as_double(f32_to_f64_bits(fl[k]));
-        if (special_float(fl[L + k])) dst[3][k] = __longlong_as_double(f32_to_f64_bits(fl[L + k]));
+        const float2 a = pa[k];
+        const float sh = a.x + a.y;
+        const float sl = a.y - (sh - a.x);
+        bool sk = false;
+        (void)pair_double_fast(sh, sl, sk);
+        if (sk) dst[0][k] = nonfinite_bits(a.x) ? nonfinite_double(a.x) : (double)sh + (double)sl;
       }
     }
   }

@@ -43,8 +43,12 @@ int main() {
               check(half <= (size_t)g.ab, "staged record halves inside the accumulators", prec, step, R, W, L, S);
               if (!step) {
                 check(g.stage_fits(), "write-out staging inside nb0", prec, step, R, W, L, S);
-                if (prec == NSI_MIXED_F32_ACC64)  // two (leading, error) float2 per entry and round
+                if (prec == NSI_MIXED_F32_ACC64) {
+                  // A pairs and G_x, G_y in nb0; G_z in the half of nb1 past the column indices
                   check((size_t)16 * L <= 4 * tb * n, "pair staging inside nb0", prec, step, R, W, L, S);
+                  check(g.nb1() + 4 * n + 4 * (size_t)L <= g.acc() && (size_t)4 * L <= 4 * n,
+                        "G_z staging inside nb1 past the column indices", prec, step, R, W, L, S);
+                }
               } else {
                 check((size_t)g.ob * L <= 4 * tb * n && (size_t)8 * L <= 4 * tb * n, "step staging inside nb0", prec,
                       step, R, W, L, S);
