@@ -32,12 +32,14 @@ _i64 = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, -O2, no fast-math)."""
+    """Compile the oracle shared library (gcc, -O2, no fast-math; OpenMP for
+    the multi-threaded assembly where the compiler has it)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -66,6 +68,8 @@ def _load():
             lib.oracle_vjp.restype = ctypes.c_int
             lib.oracle_vjp.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _d, _d, _d]
+            lib.oracle_assemble_threads.restype = ctypes.c_int
+            lib.oracle_assemble_threads.argtypes = lib.oracle_assemble.argtypes + [ctypes.c_int]
             lib.oracle_vjp_mu_abs.restype = ctypes.c_int
             lib.oracle_vjp_mu_abs.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, _d, _d]
             _lib = lib
@@ -132,6 +136,24 @@ def assemble(coord, lnods, u, un=None, rho=1.0, mu=1e-3, dt=1e-2, csr=None):
                              _p(A, _d), _p(G, _d), _p(rhs, _d))
     if rc != 0:
         raise ValueError(f"oracle_assemble failed ({rc})")
+    return row_ptr, col_idx, A, G, rhs
+
+
+def assemble_threads(coord, lnods, u, un=None, rho=1.0, mu=1e-3, dt=1e-2, csr=None, threads=0):
+    """``assemble`` on several host threads (0: all OpenMP threads); bitwise
+    equal to ``assemble`` (see ``oracle_assemble_threads``)."""
+    lib = _load()
+    coord, lnods, u = _f64(coord), _ln(lnods), _f64(u)
+    un = u if un is None else _f64(un)
+    n = coord.shape[0]
+    row_ptr, col_idx = pattern(n, lnods) if csr is None else csr
+    nnz = int(row_ptr[-1])
+    A = np.empty(nnz); G = np.empty((3, nnz)); rhs = np.empty((3, n))
+    rc = lib.oracle_assemble_threads(n, lnods.shape[0], _p(coord, _d), _p(lnods, _i32), _p(u, _d), _p(un, _d),
+                                     rho, mu, dt, _p(_ln(row_ptr), _i32), _p(_ln(col_idx), _i32),
+                                     _p(A, _d), _p(G, _d), _p(rhs, _d), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_assemble_threads failed ({rc})")
     return row_ptr, col_idx, A, G, rhs
 
 

@@ -456,3 +456,17 @@ def test_vjp_mu_abs_brute_force():
     w1 = np.sign(grad)
     _, gmu1 = oracle.vjp(X, ln1, u1, w1, 1.0, 1e-3, 1e-2)
     assert gmu1 == pytest.approx(oracle.vjp_mu_abs(X, ln1, u1, w1), rel=RTOL)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_threaded_assembly_is_bitwise_the_serial_one(threads):
+    """The multi-threaded oracle (element pass, then a row pass adding each
+    row's contributions in increasing element order) returns exactly the
+    serial oracle's arrays, on a randomly numbered, jittered mesh with a
+    separate RHS velocity."""
+    mesh, u = meshgen.config_mesh(N=6, jitter=0.15, numbering="random", seed=73)
+    un = np.random.default_rng(74).standard_normal(u.shape)
+    ref = oracle.assemble(mesh.coord, mesh.lnods, u, un, 1.0, 1e-3, 1e-2)
+    got = oracle.assemble_threads(mesh.coord, mesh.lnods, u, un, 1.0, 1e-3, 1e-2, threads=threads)
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
