@@ -181,8 +181,10 @@ def allreduce_max(x, world):
 
 
 # ------------------------------------------------------------- CPU oracle ---
-def cpu_oracle_rate(mesh, u, n_elems, repeats=3):
-    """Elements/s of the FP64 oracle (one host thread) on the first n_elems tets."""
+def cpu_oracle_rate(mesh, u, n_elems, repeats=3, threads=1):
+    """Elements/s of the FP64 oracle on the first n_elems tets: the serial
+    assembly on one host thread, or the multi-threaded one (bitwise the same
+    result) on `threads` threads (0: every host core)."""
     import oracle
 
     ln = mesh.lnods[:n_elems]
@@ -190,9 +192,20 @@ def cpu_oracle_rate(mesh, u, n_elems, repeats=3):
     times = []
     for _ in range(repeats):
         t = time.perf_counter()
-        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        if threads == 1:
+            oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        else:
+            oracle.assemble_threads(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr,
+                                    threads=threads)
         times.append(time.perf_counter() - t)
     return n_elems / statistics.median(times), statistics.median(times)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
 
 
 def run_reference(args, world, rank):
@@ -204,22 +217,29 @@ def run_reference(args, world, rank):
     n_s = min(args.ref_sample, mesh.n_elems)
     ln = mesh.lnods[:n_s]
     csr = oracle.pattern(mesh.n_nodes, ln)
+    cores = host_cores()
+
+    def one():
+        oracle.assemble_threads(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr,
+                                threads=cores)
+
     for _ in range(args.warmup):
-        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        one()
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        oracle.assemble(mesh.coord, ln, u, None, meshgen.RHO, meshgen.MU, meshgen.DT, csr=csr)
+        one()
         times.append(time.perf_counter() - t)
     ms = 1e3 * statistics.mean(times)
     value = n_s / (ms * 1e-3)
-    sample = f"first {n_s} of {mesh.n_elems} tets of the workload per step (all nodes), FP64, one host thread"
+    sample = (f"first {n_s} of {mesh.n_elems} tets of the workload per step (all nodes), FP64, "
+              f"{cores} host threads (OpenMP; bitwise the serial oracle's result)")
     line = {
         "impl": "reference", "metric": "tet elements assembled/s", "value": value, "unit": "elements/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": "fp64 oracle", "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -384,14 +404,101 @@ def run_gpu(args, world, rank, local):
         line["speedup_vs_fp64"] = results["fp64"]["ms"] / main["ms"]
     if "e2e" in main:
         line["e2e"] = main["e2e"]
+    if "fp64" in results:
+        line["fp64_roofline"] = fp64_roofline(E, results["fp64"]["kernel_ms"])
     if rank == 0 and not args.no_cpu_baseline:
         n_s = min(args.cpu_sample, E)
-        rate, med = cpu_oracle_rate(mesh, u, n_s)
-        line["cpu_baseline"] = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                                "sample": f"first {n_s} tets of the workload (all nodes), FP64, median of 3 "
-                                          f"runs of {med:.2f} s each, one host thread"}
+        cores = host_cores()
+        rate, med = cpu_oracle_rate(mesh, u, n_s, threads=cores)
+        line["cpu_baseline"] = {"value": rate, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                                "sample": f"first {n_s} tets of the workload (all nodes), FP64, median of 3 runs of "
+                                          f"{med:.2f} s each, {cores} host threads (OpenMP element pass, then a row "
+                                          f"pass in element order: bitwise the serial oracle's result)"}
+        rate1, med1 = cpu_oracle_rate(mesh, u, n_s, threads=1)
+        line["cpu_baseline_1core"] = {"value": rate1, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"the same sample, serial oracle, median of 3 runs of {med1:.2f} s"}
+    if world == 1 and not args.no_extras and args.workload == "cube100":
+        line["more_workloads"] = more_workloads(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# FP64 floating-point operations per tet of the FP64 row gather, counted from
+# its double-precision arithmetic (an FMA is 2): each element is evaluated from
+# each of its 4 rows, 96 per evaluation (two cofactor cross products 18, det 5,
+# c_i 9, 1/det by Newton-Raphson 9, the viscous factor 1, the convection-plus-
+# viscous vector w 18, the pressure-gradient vector 3, three w . c_x 15 with
+# their orientation 4, the row's accumulators 12, the determinant sum 2), plus
+# the per-row diagonal sums and edge vectors (about 20 per tet at 5.8 tets per
+# node).  The method's own count (each element once) is about 300.
+FP64_FLOPS_PER_TET = 4 * 96 + 20
+
+
+def fp64_peak():
+    """(TFLOP/s, source): cuBLAS DGEMM (4096^3, best of 3) measured in this run."""
+    import torch
+
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * n ** 3 / best / 1e12, "cuBLAS DGEMM 4096^3 measured in this run (best of 3)"
+
+
+def fp64_roofline(E, kernel_ms):
+    """FP64 mode's bound: the double-precision pipe.  achieved = the kernel's
+    FP64 operations (FP64_FLOPS_PER_TET x tets) / its time, against DGEMM."""
+    peak, src = fp64_peak()
+    achieved = FP64_FLOPS_PER_TET * E / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_tet": FP64_FLOPS_PER_TET, "kernel_ms": kernel_ms, "peak_source": src}
+
+
+def more_workloads(args):
+    """Compact records of the largest single-GPU workload (the 200^3 cube in RCM
+    numbering, 48 M tets, mixed32 and mixed64 row gather) and of the batching
+    workload (64 meshes, graph replay): ms per step, elements/s and the HBM
+    roofline fraction of the main kernel."""
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    out = {}
+    t_start = time.perf_counter()
+    mesh, u = meshgen.config_mesh("cube200_rcm")
+    E, n = mesh.n_elems, mesh.n_nodes
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    peak, _ = hbm_peak()
+    rec = {"workload": WORKLOADS["cube200_rcm"], "elements": E, "steps": 10, "modes": {}}
+    for prec in ("mixed32", "mixed64"):
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec)
+        ut = torch.as_tensor(u.T.copy()).cuda().float().contiguous()
+        o = asm.empty_outputs()
+        fn = lambda: asm.assemble(ut, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, out=o)  # noqa: E731
+        ms, kms = time_steps(asm, fn, 10, 3, lambda: flush_buf.fill_(1), stream)
+        km = statistics.mean(kms)
+        b = algorithmic_bytes(E, n, asm.nnz, prec)
+        rec["modes"][prec] = {"ms": statistics.mean(ms), "kernel_ms": km,
+                              "elements_per_s": E / (statistics.mean(ms) * 1e-3),
+                              "roofline_frac": b / (km * 1e-3) / 1e9 / peak}
+        asm.close()
+        del o
+    out["cube200_rcm"] = rec
+    del mesh, u
+    torch.cuda.empty_cache()
+    out["batch64"] = batch_record(steps=100, warmup=5, precision="mixed64", autotune=True)
+    out["seconds"] = time.perf_counter() - t_start
+    return out
 
 
 def shard_meshes(sizes, world):
@@ -407,25 +514,24 @@ def shard_meshes(sizes, world):
     return [sorted(p) for p in parts]
 
 
-def run_batch(args, world, rank, local):
-    """64 meshes per step: velocity update + batched assembly replayed from one CUDA graph.
-    With N ranks the 64 meshes are split over the ranks (no collective)."""
+def batch_time(precision, autotune, warmup, steps, world=1, rank=0):
+    """64 meshes per step: velocity update + batched assembly replayed from one
+    CUDA graph.  With N ranks the meshes are split over the ranks (no
+    collective).  Returns (ms per step, max over ranks; elements of the whole
+    batch; autotuned launch shapes; meshes on this rank)."""
     import torch
 
     import paper_2111_05651_gb300 as nsi
 
-    torch.cuda.set_device(local)
-    nsi.load_library()
     all_meshes = meshgen.batch_meshes()
     mine = shard_meshes([m.n_elems for m, _ in all_meshes], world)[rank]
     meshes = [all_meshes[i] for i in mine]
-    prec = args.precision
-    asms = [nsi.Assembler(m.coord, m.lnods, precision=prec) for m, _ in meshes]
-    vt = torch.float64 if prec == "fp64" else torch.float32
+    asms = [nsi.Assembler(m.coord, m.lnods, precision=precision) for m, _ in meshes]
+    vt = torch.float64 if precision == "fp64" else torch.float32
     base = [torch.as_tensor(u.T.copy()).cuda().to(vt) for _, u in meshes]
-    cache = os.path.join(ROOT, "paper_2111_05651_gb300", "_build", "autotune_cache.json") if args.autotune else None
+    cache = os.path.join(ROOT, "paper_2111_05651_gb300", "_build", "autotune_cache.json") if autotune else None
     tuned = {}
-    if args.autotune:
+    if autotune:
         for a, b in zip(asms, base):
             r = a.autotune(b, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, cache=cache)
             tuned[r] = tuned.get(r, 0) + 1
@@ -443,11 +549,10 @@ def run_batch(args, world, rank, local):
         for c, b in zip(cur, base):  # u(t) = u0 cos(2 pi 0.01 t): the in-graph velocity update
             c.copy_(b * torch.cos(0.06283185307179587 * step))
         nsi.assemble_batched(asms, cur, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, outs=outs)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
     E = sum(m.n_elems for m, _ in all_meshes)  # the whole batch, over all ranks
-    steps = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
@@ -458,14 +563,37 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     ms = allreduce_max(e0.elapsed_time(e1) / steps, world)
+    del graph
+    for a in asms:
+        a.close()
+    return ms, E, tuned, len(meshes)
+
+
+def batch_record(steps, warmup, precision, autotune):
+    """The batching workload as a compact record (one GPU)."""
+    ms, E, tuned, _ = batch_time(precision, autotune, warmup, steps)
+    return {"workload": WORKLOADS["batch64"], "elements": E, "precision": precision, "steps": steps,
+            "ms": ms, "elements_per_s": E / (ms * 1e-3),
+            "autotuned": {f"{k[0]}/{k[1]}": v for k, v in tuned.items()} or None}
+
+
+def run_batch(args, world, rank, local):
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    torch.cuda.set_device(local)
+    nsi.load_library()
+    prec = args.precision
+    ms, E, tuned, n_mine = batch_time(prec, args.autotune, args.warmup, args.steps, world, rank)
     if rank == 0:
         print(json.dumps({
             "metric": "tet elements assembled/s", "value": E / (ms * 1e-3), "unit": "elements/s",
-            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch64"], "meshes": len(all_meshes), "elements": E,
-                       "meshes_on_rank0": len(meshes),
-                       "precision": prec, "launches_per_step": "1 batched + 64 pack + velocity update",
+            "config": {"workload": WORKLOADS["batch64"], "meshes": 64, "elements": E,
+                       "meshes_on_rank0": n_mine,
+                       "precision": prec, "launches_per_step": "1 batched + 1 batched pack + velocity update",
                        "autotuned": {f"{k[0]}/{k[1]}": v for k, v in tuned.items()} or None,
                        "l2": "working set (outputs of all meshes) > L2; no flush between replays"},
         }), flush=True)
@@ -618,9 +746,10 @@ def main():
     ap.add_argument("--precision", default="mixed64", choices=["fp64", "mixed64", "mixed32"])
     ap.add_argument("--scatter", default="auto", choices=["auto", "gather", "color", "atomic"])
     ap.add_argument("--cpu-sample", type=int, default=3_000_000)
-    ap.add_argument("--ref-sample", type=int, default=500_000)
+    ap.add_argument("--ref-sample", type=int, default=3_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 200^3 and batch64 records of the default run")
     ap.add_argument("--quick", action="store_true", help="time only the main precision")
     ap.add_argument("--autotune", action="store_true", help="batch64: autotune launch shapes (cached)")
     ap.add_argument("--fan", action="store_true", help="row gather through the edge-fan kernel")
