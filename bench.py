@@ -312,6 +312,8 @@ def run_gpu(args, world, rank, local):
         asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec, scatter=args.scatter)
         if args.fan:
             nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
+        if args.atomic_agg:
+            nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_ATOMIC, 1)
         vt = torch.float64 if prec == "fp64" else torch.float32
         ut = torch.as_tensor(u.T.copy()).to(dev, vt).contiguous()
         out = asm.empty_outputs()
@@ -720,6 +722,8 @@ def run_profile(args):
         asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec, scatter=args.scatter)
         if args.fan:
             nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_GATHER, -1)
+        if args.atomic_agg:
+            nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_ATOMIC, 1)
         vt = torch.float64 if prec == "fp64" else torch.float32
         ut = torch.as_tensor(u.T.copy()).cuda().to(vt)
         if args.profile_step:  # the cached-geometry time step: A_static once, then 3 steps
@@ -753,6 +757,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="time only the main precision")
     ap.add_argument("--autotune", action="store_true", help="batch64: autotune launch shapes (cached)")
     ap.add_argument("--fan", action="store_true", help="row gather through the edge-fan kernel")
+    ap.add_argument("--atomic-agg", action="store_true", help="atomic scatter with warp-aggregated atomics")
     ap.add_argument("--profile-step", action="store_true", help="--profile-run times the cached-geometry step")
     ap.add_argument("--profile-run", default=None, metavar="PRECS",
                     help="no timing: 3 assembly calls per listed precision (for ncu)")

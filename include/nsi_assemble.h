@@ -291,20 +291,25 @@ nsi_status nsi_device_status(NsiHandle* h, void* stream);
 /*
  * Launch autotuner (project-written): times every available launch choice on
  * this mesh with the given fields and outputs -- the row-gather kernel at each
- * rows-per-block shape that fits shared memory, the colouring kernel and the
- * atomic kernel, and the edge-fan row-gather kernel where the mesh has its map
- * -- `reps` calls each after one warm-up call, keeps the fastest as the
- * handle's default, and reports it (chosen_rows as in nsi_set_launch).
+ * rows-per-block shape that fits shared memory, the colouring kernel, the
+ * atomic kernel with and without warp aggregation, and the edge-fan
+ * row-gather kernel where the mesh has its map -- `reps` calls each after one
+ * warm-up call, keeps the fastest as the handle's default, and reports it
+ * (chosen_rows as in nsi_set_launch; 0 for colouring).
  * Synchronises `stream`; overwrites the outputs.  Either output may be NULL.
  */
 nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t reps, void* stream,
                         int32_t* chosen_scatter, int32_t* chosen_rows);
 
 /*
- * Set the handle's default scatter mode and row-gather kernel: rows_per_block
- * > 0 selects the per-row star kernel with that many rows per block, -1 the
- * edge-fan kernel (one thread per CSR entry), 0 keeps the current choice; e.g.
- * to apply a cached autotuning result.
+ * Set the handle's default scatter mode and its kernel, e.g. to apply a cached
+ * autotuning result.  With NSI_SCATTER_GATHER (or AUTO), rows_per_block > 0
+ * selects the per-row star kernel with that many rows per block, -1 the
+ * edge-fan kernel (one thread per CSR entry), 0 keeps the current choice.
+ * With NSI_SCATTER_ATOMIC, rows_per_block 1 selects warp-aggregated atomics
+ * (lanes adding to the same entry combine their values by shuffles and issue
+ * one atomic), 2 one atomic per value (the default), 0 keeps the choice.
+ * (Defined by this library's design; the paper's scatter is the host's.)
  */
 nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block);
 

@@ -66,6 +66,7 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->walk_ptr);
   cudaFree(h->walk);
   cudaFree(h->diag_pos);
+  cudaFree(h->elem_pos);
   cudaFree(h->exact_list);
   cudaFree(h->exact_ptr);
   cudaFree(h->exact_inc);
@@ -388,6 +389,30 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     });
   }
 
+  // 4.5 element-position map for the element-centric kernels (colouring,
+  //     atomics): the row position of every other node of each element
+  const bool pos_ok = max_row <= STAR_MAX_ROW;
+  std::vector<unsigned long long> elem_pos;
+  if (pos_ok) {
+    elem_pos.assign(E, 0ull);
+    parallel_for(E, [&](int64_t lo, int64_t hi) {
+      for (int64_t e = lo; e < hi; ++e) {
+        const int32_t* v = &ln[4 * e];
+        unsigned long long w = 0;
+        for (int a = 0; a < 4; ++a) {
+          const int32_t* c = &col[rp64[v[a]]];
+          const int64_t len = row_len[v[a]];
+          for (int b = 0; b < 4; ++b) {
+            if (b == a) continue;
+            const unsigned long long q = (unsigned long long)(std::lower_bound(c, c + len, v[b]) - c);
+            w |= q << (ELEM_POS_BITS * elem_pos_slot(a, b));
+          }
+        }
+        elem_pos[e] = w;
+      }
+    });
+  }
+
   // 4a. every row's element walk (the order and steps of the kernel's element loop)
   std::vector<int32_t> walk_ptr;
   std::vector<uint8_t> walk;
@@ -659,7 +684,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   if (h->gather_ok) {
     if ((st = dev_upload(h, &h->walk_ptr, walk_ptr.data(), n + 1, s))) return st;
     if ((st = dev_upload(h, &h->walk, walk.data(), walk.size(), s))) return st;
+  }
+  if (pos_ok) {
     if ((st = dev_upload(h, &h->diag_pos, diag.data(), n, s))) return st;
+    if ((st = dev_upload(h, &h->elem_pos, elem_pos.data(), E, s))) return st;
   }
   if (h->exact_rows > 0) {
     if ((st = dev_upload(h, &h->exact_list, exact_list.data(), exact_list.size(), s))) return st;
@@ -788,7 +816,12 @@ nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block)
   if (!h) return fail(NSI_ERR_INVALID_ARG, "handle is NULL");
   if (scatter < NSI_SCATTER_AUTO || scatter > NSI_SCATTER_GATHER) return fail(NSI_ERR_INVALID_ARG, "unknown scatter mode");
   if (scatter == NSI_SCATTER_GATHER && !h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode not available for this mesh");
-  if (rows_per_block == -1) {
+  if (scatter == NSI_SCATTER_ATOMIC) {
+    // the atomic kernel: 1 warp-aggregated, 2 one atomic per value, 0 unchanged
+    if (rows_per_block < 0 || rows_per_block > 2)
+      return fail(NSI_ERR_INVALID_ARG, "for the atomic mode, rows_per_block is 0, 1 or 2");
+    if (rows_per_block) h->atomic_agg = rows_per_block == 1;
+  } else if (rows_per_block == -1) {
     if (!h->fan_ok) return fail(NSI_ERR_UNSUPPORTED, "no edge-fan map for this mesh");
     h->use_fan = true;
   } else if (rows_per_block != 0) {

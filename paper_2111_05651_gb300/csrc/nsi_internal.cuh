@@ -50,6 +50,15 @@ constexpr unsigned WALK_ELEM = 1u << 5;  // the step evaluates element (p, q, c)
 constexpr unsigned WALK_NEG = 1u << 6;   // (p, q, c) is an odd permutation of the element's order
 constexpr unsigned WALK_EVQ = 1u << 7;   // q leaves (next window (p, c)); else p leaves (next window (q, c))
 
+// Element-position map, for the element-centric kernels: per element one
+// 64-bit word holding, for every ordered pair (a, b) of its local nodes with
+// b != a, the position of node b inside the CSR row of node a, 5 bits each,
+// at bit 5 * (3a + (b < a ? b : b - 1)); the diagonal positions come from
+// diag_pos.  Built for meshes whose rows have at most 32 entries (others scan
+// the row).
+constexpr int ELEM_POS_BITS = 5;
+__host__ __device__ inline int elem_pos_slot(int a, int b) { return 3 * a + (b < a ? b : b - 1); }
+
 // Edge-fan map: for every off-diagonal CSR entry (i, j), the ring of nodes
 // around the edge (i, j) -- the other two nodes of every element containing
 // both i and j, chained in cyclic order so that consecutive ring nodes k, l
@@ -154,13 +163,15 @@ struct NsiHandle {
   // row-gather map: every row's element walk (one byte per step)
   int32_t* walk_ptr = nullptr;  // [n+1]
   uint8_t* walk = nullptr;      // [walk_ptr[n] + 8]
-  uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row
+  uint8_t* diag_pos = nullptr;  // [n] position of the diagonal inside its row (rows <= 32 entries)
+  unsigned long long* elem_pos = nullptr;  // [E] element-position map (rows <= 32 entries), or null
   // edge-fan map (one word per CSR entry) and its block partition of the rows
   bool fan_ok = false;
   uint32_t* fan = nullptr;      // [nnz]
   int32_t* fan_blk = nullptr;   // [fan_blocks + 1] first row of every fan block
   int64_t fan_blocks = 0;
   bool use_fan = false;         // row-gather mode runs the edge-fan kernel
+  bool atomic_agg = false;      // atomic mode runs the warp-aggregated atomics (else one atomic per value)
   bool persistent = false;      // row-gather mode runs the persistent grid (set by create: mixed64)
   int64_t exact_rows = 0;       // mixed modes: rows recomputed in double (badly shaped elements)
   int32_t* exact_list = nullptr;  // [exact_rows] their node ids

@@ -211,6 +211,8 @@ def test_autotune_choice_and_cache(tmp_path):
     assert sc in ("gather", "color", "atomic")
     if sc == "gather":
         assert rows in (-1, 32, 64, 96, 128)
+    elif sc == "atomic":
+        assert rows in (1, 2)  # warp-aggregated or one atomic per value
     out = asm.assemble(ut)
     torch.cuda.synchronize()
     for a, b in zip(out, ref):

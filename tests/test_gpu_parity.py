@@ -109,6 +109,40 @@ def test_integer_valued_assembly_is_exact(precision, scatter):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_warp_aggregated_atomics(precision):
+    """The atomic scatter with warp aggregation (nsi_set_launch(ATOMIC, 1)):
+    same results as the oracle within the precision's bar on a randomly
+    numbered jittered mesh and a Delaunay mesh, and the exact integers of the
+    integer lattice in FP64 and mixed64 (the lanes' partial sums are formed in
+    the output type)."""
+    for mesh, u in (meshgen.config_mesh(N=9, jitter=0.15, numbering="random", seed=91),
+                    meshgen.delaunay_cube(m=7, jitter=0.3, seed=92)):
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter="atomic")
+        nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_ATOMIC, 1)
+        A, G, rhs = (t.double().cpu().numpy() for t in asm.assemble(torch.as_tensor(u.T.copy())))
+        rp = asm.pattern()[0].cpu().numpy()
+        asm.close()
+        orp, oci, oA, oG, orhs = _oracle(mesh, u, precision)
+        np.testing.assert_array_equal(rp, orp)
+        err = errors(rp, A, G, rhs, oA, oG, orhs)
+        assert max(err.values()) <= TOL[precision], err
+    if precision != "mixed32":
+        N = 7
+        mesh, _ = meshgen.config_mesh(N=N, numbering="random", seed=86)
+        coord = np.rint(mesh.coord * N)
+        rng = np.random.default_rng(87)
+        u = rng.integers(-2**19, 2**19, size=(mesh.n_nodes, 3)).astype(np.float64)
+        rho, mu, dt = 120.0, 0.0, 5.0 / 2**20
+        _, _, oA, _, orhs = oracle.assemble(coord, mesh.lnods, u, None, rho, mu, dt)
+        asm = nsi.Assembler(coord, mesh.lnods, precision=precision, scatter="atomic")
+        nsi.nsi_set_launch(asm.handle, nsi.NSI_SCATTER_ATOMIC, 1)
+        A, _, rhs = asm.assemble(torch.as_tensor(u.T.copy()), rho=rho, mu=mu, dt=dt)
+        np.testing.assert_array_equal(A.cpu().numpy(), np.rint(oA))
+        np.testing.assert_array_equal(rhs.cpu().numpy(), np.rint(orhs))
+        asm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
 @pytest.mark.parametrize("bad", [np.nan, np.inf], ids=["nan", "inf"])
 def test_nonfinite_velocity_propagates(precision, bad):
     """A NaN or infinite velocity at one node makes the A entries and the RHS
