@@ -66,7 +66,7 @@
 extern "C" {
 #endif
 
-#define NSI_ABI_VERSION 1
+#define NSI_ABI_VERSION 2
 
 typedef struct NsiHandle NsiHandle; /* opaque; one per mesh */
 
@@ -92,7 +92,8 @@ typedef enum {
     NSI_SCATTER_COLOR = 1,    /* element colouring, plain read-add-write, deterministic */
     NSI_SCATTER_ATOMIC = 2,   /* one element per thread, global atomic adds */
     NSI_SCATTER_GATHER = 3    /* one CSR row per thread, gathers its elements, writes once;
-                                 deterministic; rows of at most 32 entries */
+                                 deterministic (rows of more than 32 entries by a second,
+                                 per-row kernel: NsiInfo.long_rows) */
 } nsi_scatter;
 
 typedef struct {
@@ -170,6 +171,11 @@ typedef struct {
                                time step these rows are recomputed in double from the coordinates
                                and overwritten (a float determinant of such an element carries
                                about that ratio times the float rounding of its edge vectors) */
+    int32_t long_rows;      /* rows the row gather leaves out -- more than 32 entries (its walk
+                               steps hold five bits of row position), or a star its walk
+                               encoder could not cover -- computed after every row-gather
+                               assembly or time step by one thread per row, in double; the rest
+                               of the mesh stays on the row gather */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 

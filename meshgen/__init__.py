@@ -36,7 +36,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "kuhn_cube", "jitter_interior", "renumber", "random_permutation",
-    "rcm_permutation", "sinusoid_velocity", "add_noise", "gaussian_weights",
+    "rcm_permutation", "sinusoid_velocity", "add_noise", "gaussian_weights", "delaunay_hub",
     "config_mesh", "batch_meshes", "delaunay_cube", "CONFIGS",
 ]
 
@@ -230,6 +230,39 @@ def delaunay_cube(m: int = 8, jitter: float = 0.25, seed: int = 5):
     T[vol6 < 0] = T[vol6 < 0][:, [0, 1, 3, 2]]
     mesh = Mesh(coord=P, lnods=T.astype(np.int32), N=m, meta={"kind": "delaunay_cube", "m": m, "jitter": jitter,
                                                             "seed": seed})
+    u = sinusoid_velocity(P, rng)
+    return mesh, np.ascontiguousarray(u)
+
+
+def delaunay_hub(m: int = 4, k: int = 48, radius: float = 0.3, seed: int = 6):
+    """(mesh, u): an unstructured mesh of the unit cube with one node of very
+    high valence -- the Delaunay tetrahedralization (scipy / Qhull) of the
+    (m+1)^3 lattice, minus its points within `radius` of the centre, plus the
+    centre itself and k points spread evenly over the sphere of that radius
+    around it (a Fibonacci lattice, seeded rotation).  Every sphere point is a
+    Delaunay neighbour of the centre, so the centre's row has about k + 1
+    entries.  Flat tets are dropped and tets listed with positive orientation,
+    as delaunay_cube.  u: the seeded sinusoids, as config_mesh."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    g = np.arange(m + 1, dtype=np.float64) / m
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    c = np.full(3, 0.5)
+    P = P[np.linalg.norm(P - c, axis=1) > 1.2 * radius]
+    i = np.arange(k) + 0.5
+    phi = np.arccos(1.0 - 2.0 * i / k)
+    theta = np.pi * (1.0 + 5.0 ** 0.5) * i + rng.uniform(0.0, 2.0 * np.pi)
+    S = c + radius * np.stack([np.cos(theta) * np.sin(phi), np.sin(theta) * np.sin(phi), np.cos(phi)], 1)
+    P = np.vstack([P, c[None, :], S])
+    T = Delaunay(P).simplices.astype(np.int64)
+    X = P[T]
+    vol6 = np.linalg.det(X[:, 1:] - X[:, :1])
+    keep = np.abs(vol6) > 1e-9 / m ** 3
+    T, vol6 = T[keep], vol6[keep]
+    T[vol6 < 0] = T[vol6 < 0][:, [0, 1, 3, 2]]
+    mesh = Mesh(coord=np.ascontiguousarray(P), lnods=T.astype(np.int32), N=m,
+                meta={"kind": "delaunay_hub", "m": m, "k": k, "radius": radius, "seed": seed})
     u = sinusoid_velocity(P, rng)
     return mesh, np.ascontiguousarray(u)
 

@@ -77,7 +77,8 @@ class NsiInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("n_colors", ctypes.c_int32), ("max_row", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("scatter", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("rows_per_block", ctypes.c_int32),
-                ("n_plans", ctypes.c_int32), ("persistent", ctypes.c_int32), ("exact_rows", ctypes.c_int32)]
+                ("n_plans", ctypes.c_int32), ("persistent", ctypes.c_int32), ("exact_rows", ctypes.c_int32),
+                ("long_rows", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -68,6 +68,9 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->diag_pos);
   cudaFree(h->elem_pos);
   cudaFree(h->exact_list);
+  cudaFree(h->long_list);
+  cudaFree(h->long_ptr);
+  cudaFree(h->long_inc);
   cudaFree(h->exact_ptr);
   cudaFree(h->exact_inc);
   cudaFree(h->fan);
@@ -363,12 +366,15 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     }
   });
 
-  // 4. row-gather map (positions of the other three nodes in the row)
-  h->gather_ok = max_row <= STAR_MAX_ROW;
+  // 4. row-gather map (positions of the other three nodes in the row).  Rows
+  //    of more than 32 entries (five bits of row position) are "long rows":
+  //    the row gather leaves them out and long_rows_kernel computes them.
+  h->gather_ok = inc_ptr[n] <= INT32_MAX;
   std::vector<uint16_t> star;
   std::vector<uint8_t> diag(n, 0);
+  std::vector<uint8_t> is_long(n, 0);
+  for (int64_t i = 0; i < n; ++i) is_long[i] = row_len[i] > STAR_MAX_ROW;
   if (h->gather_ok) {
-    if (inc_ptr[n] > INT32_MAX) return fail(NSI_ERR_UNSUPPORTED, "too many element-node incidences");
     star.resize(inc_ptr[n]);
     // even permutations of (0,1,2,3) that bring vertex a to the front
     static const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
@@ -376,6 +382,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
       for (int64_t i = lo; i < hi; ++i) {
         const int32_t* c = &col[rp64[i]];
         int64_t len = row_len[i];
+        if (is_long[i]) {
+          diag[i] = DIAG_LONG;
+          continue;
+        }
         auto pos = [&](int32_t j) { return (int)(std::lower_bound(c, c + len, j) - c); };
         diag[i] = len ? (uint8_t)pos((int32_t)i) : 0;
         for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) {
@@ -426,7 +436,12 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
       WalkWork ws;
       for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); ++i) {
         const size_t before = buf.size();
-        if (!encode_walk(&star[inc_ptr[i]], (int)(inc_ptr[i + 1] - inc_ptr[i]), diag[i], buf, ws)) bad = true;
+        if (!is_long[i] && !encode_walk(&star[inc_ptr[i]], (int)(inc_ptr[i + 1] - inc_ptr[i]), diag[i], buf, ws)) {
+          // a star the encoder cannot walk: the row becomes a long row
+          buf.resize(before);
+          is_long[i] = 1;
+          diag[i] = DIAG_LONG;
+        }
         wlen[i] = (int32_t)(buf.size() - before);
       }
       std::lock_guard<std::mutex> g(mu);
@@ -452,7 +467,8 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   // 4b. edge-fan map: per off-diagonal entry (i, j) the ring of nodes around the edge
   std::vector<uint32_t> fan;
   std::vector<int32_t> fan_blk;
-  h->fan_ok = h->gather_ok && max_row <= FAN_MAX_ROW;
+  h->fan_ok = h->gather_ok && max_row <= FAN_MAX_ROW &&
+              std::find(is_long.begin(), is_long.end(), (uint8_t)1) == is_long.end();
   if (h->fan_ok) {
     fan.assign(nnz, 0u);
     std::atomic<bool> bad{false};
@@ -590,8 +606,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     // a tie the smallest block, whose barriers hold fewer warps
     const size_t smem_sm = 228 * 1024, smem_max = 200 * 1024;
     const int regs = std::max(32, gather_kernel_regs(h->precision));
-    const int W = std::max(1, (int)max_row);
-    int chosen = 0, chosen_L = 0, chosen_S = 0, best_warps = 0;
+    int64_t short_max = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (!is_long[i]) short_max = std::max(short_max, row_len[i]);
+    int chosen = 0, best_warps = 0;
     for (int R : {32, 64, 96, 128}) {
       if (!h->gather_ok) break;
       int64_t mL = 0, mS = 0;
@@ -600,6 +618,9 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
         mL = std::max<int64_t>(mL, rp64[r1] - rp64[r0]);
         mS = std::max<int64_t>(mS, walk_ptr[r1] - walk_ptr[r0]);
       }
+      // slots per row: the longest row the kernel takes, or more where a
+      // block's long rows would not leave room for its entries in R * w
+      const int W = (int)std::max<int64_t>({1, short_max, (mL + R - 1) / R});
       const GatherSmem g = gather_smem(h->precision, R, W, (int)mL, (int)mS);
       const size_t sm = g.total();
       if (sm > smem_max || !g.stage_fits()) continue;
@@ -610,20 +631,16 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
       cand.rows_per_block = R;
       cand.max_block_entries = (int)mL;
       cand.max_block_steps = (int)mS;
+      cand.w = W;
       cand.n_blocks = (n + R - 1) / R;
       h->plans[h->n_plans++] = cand;
       if (warps > best_warps) {
         best_warps = warps;
-        chosen = R;
-        chosen_L = (int)mL;
-        chosen_S = (int)mS;
+        chosen = h->n_plans - 1;
       }
     }
-    if (chosen == 0) h->gather_ok = false;
-    h->plan.rows_per_block = chosen;
-    h->plan.max_block_entries = chosen_L;
-    h->plan.max_block_steps = chosen_S;
-    h->plan.n_blocks = chosen ? (n + chosen - 1) / chosen : 0;
+    if (best_warps == 0) h->gather_ok = false;
+    else h->plan = h->plans[chosen];
     // the persistent grid (next block's phase 0 under the current block's
     // write-out) measured faster for mixed64 only: 0.505 against 0.545 ms at
     // the 100^3 cube; mixed32 unchanged, FP64 slower (4.23 against 3.29 ms)
@@ -667,6 +684,23 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if (E > (int64_t)(UINT32_MAX >> 2)) h->exact_rows = 0;  // not encodable: keep the float results
   }
 
+  // 7c. long rows: every incident element of each (element * 4 + local index)
+  std::vector<int32_t> long_list, long_ptr;
+  std::vector<uint32_t> long_inc;
+  if (h->gather_ok) {
+    for (int64_t i = 0; i < n; ++i)
+      if (is_long[i]) long_list.push_back((int32_t)i);
+    long_ptr.assign(long_list.size() + 1, 0);
+    for (size_t r = 0; r < long_list.size(); ++r) {
+      const int64_t i = long_list[r];
+      for (int64_t t = inc_ptr[i]; t < inc_ptr[i + 1]; ++t) long_inc.push_back((uint32_t)inc[t]);
+      long_ptr[r + 1] = (int32_t)long_inc.size();
+    }
+    if (!long_list.empty() && (E > (int64_t)(UINT32_MAX >> 2) || long_inc.size() > (size_t)INT32_MAX))
+      h->gather_ok = false;
+    h->long_rows = h->gather_ok ? (int64_t)long_list.size() : 0;
+  }
+
   // 8. upload
   nsi_status st;
   if ((st = dev_upload(h, &h->row_ptr, row_ptr.data(), n + 1, s))) return st;
@@ -685,9 +719,16 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->walk_ptr, walk_ptr.data(), n + 1, s))) return st;
     if ((st = dev_upload(h, &h->walk, walk.data(), walk.size(), s))) return st;
   }
-  if (pos_ok) {
+  if (pos_ok || h->gather_ok) {
     if ((st = dev_upload(h, &h->diag_pos, diag.data(), n, s))) return st;
+  }
+  if (pos_ok) {
     if ((st = dev_upload(h, &h->elem_pos, elem_pos.data(), E, s))) return st;
+  }
+  if (h->long_rows > 0) {
+    if ((st = dev_upload(h, &h->long_list, long_list.data(), long_list.size(), s))) return st;
+    if ((st = dev_upload(h, &h->long_ptr, long_ptr.data(), long_ptr.size(), s))) return st;
+    if ((st = dev_upload(h, &h->long_inc, long_inc.data(), long_inc.size(), s))) return st;
   }
   if (h->exact_rows > 0) {
     if ((st = dev_upload(h, &h->exact_list, exact_list.data(), exact_list.size(), s))) return st;
@@ -809,6 +850,7 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->n_plans = h->n_plans;
   info->persistent = h->persistent && !h->use_fan ? 1 : 0;
   info->exact_rows = (int32_t)std::min<int64_t>(h->exact_rows, INT32_MAX);
+  info->long_rows = (int32_t)std::min<int64_t>(h->long_rows, INT32_MAX);
   return NSI_OK;
 }
 

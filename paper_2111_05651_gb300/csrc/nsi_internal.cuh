@@ -82,8 +82,15 @@ struct GatherPlan {
   int rows_per_block = 0;     // threads per block = rows per block
   int max_block_entries = 0;  // max over blocks of the CSR entries of the block's rows
   int max_block_steps = 0;    // max over blocks of the walk steps of the block's rows
+  int w = 0;                  // slots per row of the layout (>= the longest row the kernels take, and
+                              // large enough that every block's entries fit R * w)
   int64_t n_blocks = 0;
 };
+
+// diag_pos value of a row the row gather leaves out ("long row": more than
+// 32 entries, or a star whose walk does not encode): the kernels give it no
+// elements and zero its slice; long_rows_kernel computes it afterwards
+constexpr uint8_t DIAG_LONG = 0xff;
 
 // Shared-memory layout of one row-gather block: R rows (one per thread), W
 // slots per row (the longest row of the mesh), L CSR entries and S walk
@@ -173,6 +180,10 @@ struct NsiHandle {
   bool use_fan = false;         // row-gather mode runs the edge-fan kernel
   bool atomic_agg = false;      // atomic mode runs the warp-aggregated atomics (else one atomic per value)
   bool persistent = false;      // row-gather mode runs the persistent grid (set by create: mixed64)
+  int64_t long_rows = 0;        // rows the row gather leaves out, recomputed by long_rows_kernel
+  int32_t* long_list = nullptr;  // [long_rows] their node ids
+  int32_t* long_ptr = nullptr;   // [long_rows + 1] into long_inc
+  uint32_t* long_inc = nullptr;  // element * 4 + local index of the row's node
   int64_t exact_rows = 0;       // mixed modes: rows recomputed in double (badly shaped elements)
   int32_t* exact_list = nullptr;  // [exact_rows] their node ids
   int32_t* exact_ptr = nullptr;   // [exact_rows + 1] into exact_inc

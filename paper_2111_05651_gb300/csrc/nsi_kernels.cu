@@ -882,6 +882,7 @@ struct BlockRows {
   int64_t i;
   int32_t base;
   V3<T> uni;
+  int zl;  // a long row's entries (its slice is zeroed in the write-out; 0 for the others)
 };
 
 // Phase 0 of a block: its bounds and the row's scalars (plain loads, in
@@ -892,7 +893,7 @@ struct Phase0 {
   int64_t r0;
   int nrows, L, S;
   int32_t base, sbase, rs, re, s0, s1;
-  int dp;
+  int dp, zl;
   V3<T> uni;
 };
 
@@ -910,7 +911,7 @@ __device__ __forceinline__ Phase0<typename Prec<P>::T> load_phase0(const MeshVie
   p.sbase = m.walk_ptr[r0];
   p.S = m.walk_ptr[r_end] - p.sbase;
   p.rs = p.re = p.s0 = p.s1 = 0;
-  p.dp = 0;
+  p.dp = p.zl = 0;
   p.uni = V3<T>{T(0), T(0), T(0)};
   const int soff = p.sbase & 3;  // walk bytes are copied as aligned 4-byte words
   if (t < p.nrows) {
@@ -921,6 +922,12 @@ __device__ __forceinline__ Phase0<typename Prec<P>::T> load_phase0(const MeshVie
     p.s1 = m.walk_ptr[i + 1] - p.sbase + soff;
     p.dp = m.diag_pos[i];
     p.uni = load_vec<T>(f.un, i);
+    if (p.dp == DIAG_LONG) {  // left to long_rows_kernel: no elements, a zeroed slice
+      p.zl = p.re - p.rs;
+      p.re = p.rs;
+      p.s1 = p.s0;
+      p.dp = 0;
+    }
   }
   return p;
 }
@@ -1020,7 +1027,7 @@ __device__ __forceinline__ bool stage_records(const MeshView& m, unsigned char* 
       }
     }
   }
-  b = BlockRows<T>{R, t, p.nrows, p.L, len, lb, p.s0, p.s1, p.dp, p.r0 + t, p.base, p.uni};
+  b = BlockRows<T>{R, t, p.nrows, p.L, len, lb, p.s0, p.s1, p.dp, p.r0 + t, p.base, p.uni, p.zl};
   return true;
 }
 
@@ -1136,6 +1143,8 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
         stage[2 * L + lb + q] = v.z;
         stage[3 * L + lb + q] = v.w;
       }
+      for (int q = 0; q < b.zl; ++q)  // a long row: its slice zeroed here, computed later
+        stage[lb + q] = stage[L + lb + q] = stage[2 * L + lb + q] = stage[3 * L + lb + q] = Out(0);
     }
     __syncthreads();
     for (int k = t; k < L; k += R) {
@@ -1164,6 +1173,10 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
         gx[lb + q] = h.x;
         gy[lb + q] = h.y;
         gz[lb + q] = h.z;
+      }
+      for (int q = 0; q < b.zl; ++q) {  // a long row: its slice zeroed here, computed later
+        pa[lb + q] = make_float2(0.f, 0.f);
+        gx[lb + q] = gy[lb + q] = gz[lb + q] = 0.f;
       }
     }
     __syncthreads();
@@ -1450,12 +1463,15 @@ __device__ __forceinline__ void step_block(const MeshView& m, const FieldView& f
     if constexpr (P == NSI_MIXED_F32_ACC64) {
       float2* stage = reinterpret_cast<float2*>(smem + lay.nb0());
       bool nonfinite = false;  // as in the assembly's write-out
-      if (t < b.nrows)
+      if (t < b.nrows) {
         for (int q = 0; q < b.len; ++q) {
           const float2 v = acc.load1(q * R + t);
           stage[b.lb + q] = v;
           nonfinite |= nonfinite_bits(v.x);
         }
+        // a long row: A_static kept here (C = 0), the convection added later
+        for (int q = 0; q < b.zl; ++q) stage[b.lb + q] = make_float2(0.f, 0.f);
+      }
       const bool fix = __syncthreads_or(nonfinite);
 #pragma unroll 2
       for (int k = t; k < b.L; k += R) A[k] = stat[k] + pair_double(stage[k].x, stage[k].y);
@@ -1464,8 +1480,10 @@ __device__ __forceinline__ void step_block(const MeshView& m, const FieldView& f
           if (nonfinite_bits(stage[k].x)) A[k] = stat[k] + nonfinite_double(stage[k].x);
     } else {
       Out* stage = reinterpret_cast<Out*>(smem + lay.nb0());
-      if (t < b.nrows)
+      if (t < b.nrows) {
         for (int q = 0; q < b.len; ++q) stage[b.lb + q] = acc.load1(q * R + t);
+        for (int q = 0; q < b.zl; ++q) stage[b.lb + q] = Out(0);  // a long row (as above)
+      }
       __syncthreads();
 #pragma unroll 2
       for (int k = t; k < b.L; k += R) A[k] = stat[k] + stage[k];
@@ -1615,6 +1633,135 @@ __global__ void __launch_bounds__(64) exact_rows_kernel(MeshView m, FieldView f,
       Ao[q] = (Out)acc[q][0];
       for (int d = 0; d < 3; ++d) Go[d * m.nnz + q] = (Out)(-acc[q][d + 1] / 24.0);
     }
+  }
+}
+
+// ---------------------------------------------------------- long rows ---
+// Rows the row gather leaves out (more than 32 entries, whose row positions
+// do not fit the walk's five bits, or a star the walk encoder could not
+// cover), computed after the kernels by one thread per row, in double (the
+// coordinates of the handle's copy, the velocities as given): every
+// off-diagonal entry (i, j) sums the contributions of the row's elements that
+// contain j, w . c_j and -c_i / 24 (with i first and the element's other
+// nodes in an even order, so that det > 0); the diagonal follows from the
+// partition of unity as in the row gather, A(i,i) = lumped mass - sum_{j != i}
+// A(i,j) and G(i,i) = 1/3 sum_{j != i} G(i,j).  MODE 0: A, G and rhs; 1: the
+// time step, A = A_static + C(u) (A may alias A_static: each entry is read
+// before it is written, by this thread) and rhs; 2: rhs, dt_rho and
+// mass_rho.  The row's elements are scanned once per entry: the rows are few.
+template <int P, int MODE>
+__global__ void __launch_bounds__(64) long_rows_kernel(MeshView m, FieldView f, const void* A_static, void* A,
+                                                       void* G, void* rhs, void* dt_rho, void* mass_rho, double kmr,
+                                                       const int32_t* rows, const int32_t* ptr, const uint32_t* inc,
+                                                       int64_t count) {
+  using Out = typename Prec<P>::Out;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const int64_t i = rows[r];
+  const int32_t rs = m.row_ptr[i], len = m.row_ptr[i + 1] - rs;
+  const int32_t* cols = m.col_idx + rs;
+  auto coord = [&](int64_t j) {
+    if constexpr (P == NSI_FP64) {
+      const D4 x = m.xyz64[j];
+      return V3<double>{x.x, x.y, x.z};
+    } else {
+      const float4 h = m.xyz_hi[j], l = m.xyz_lo[j];
+      return V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+    }
+  };
+  auto vel = [&](const void* const* comp, int64_t j) {
+    if constexpr (P == NSI_FP64) return load_vec<double>(comp, j);
+    else {
+      const V3<float> w = load_vec<float>(comp, j);
+      return V3<double>{w.x, w.y, w.z};
+    }
+  };
+  // even permutations of (0,1,2,3) that bring vertex a to the front
+  const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
+  const V3<double> xi = coord(i), ui = vel(f.u, i);
+  // one element of the row: its other nodes in even order, their edge vectors
+  // from node i, cofactors c[0..2] = det(J) grad N of those nodes, c_i, det
+  struct El {
+    int v[3];
+    V3<double> c[3], ci;
+    double det;
+    V3<double> w;  // rho/120 (2 u_i + sum of the others) + (MODE 0) mu/(6 det) c_i
+  };
+  auto element = [&](int32_t t) {
+    El el;
+    const int64_t e = inc[t] >> 2;
+    const int a = (int)(inc[t] & 3u);
+    const int4 v4 = m.lnods[e];
+    const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+    V3<double> d[3], us{2.0 * ui.x, 2.0 * ui.y, 2.0 * ui.z};
+    for (int b = 0; b < 3; ++b) {
+      el.v[b] = v[EVEN[a][b]];
+      d[b] = sub(coord(el.v[b]), xi);
+      us = add(us, vel(f.u, el.v[b]));
+    }
+    el.c[0] = cross(d[1], d[2]);
+    el.c[1] = cross(d[2], d[0]);
+    el.c[2] = cross(d[0], d[1]);
+    el.det = dot(d[0], el.c[0]);
+    el.ci = V3<double>{-(el.c[0].x + el.c[1].x + el.c[2].x), -(el.c[0].y + el.c[1].y + el.c[2].y),
+                       -(el.c[0].z + el.c[1].z + el.c[2].z)};
+    const double kv = MODE == 0 ? f.kmu / el.det : 0.0;
+    el.w = V3<double>{f.kc * us.x + kv * el.ci.x, f.kc * us.y + kv * el.ci.y, f.kc * us.z + kv * el.ci.z};
+    return el;
+  };
+  double detsum = 0.0;
+  for (int32_t t = ptr[r]; t < ptr[r + 1]; ++t) detsum += element(t).det;
+  if constexpr (MODE != 2) {
+    Out* Ao = static_cast<Out*>(A) + rs;
+    const Out* As = MODE == 1 ? static_cast<const Out*>(A_static) + rs : nullptr;
+    Out* Go = MODE == 0 ? static_cast<Out*>(G) + rs : nullptr;
+    double sa = 0.0, sg[3] = {0.0, 0.0, 0.0};
+    int dpos = 0;
+    for (int q = 0; q < len; ++q) {
+      const int32_t j = cols[q];
+      if (j == i) {
+        dpos = q;
+        continue;
+      }
+      double a = 0.0, g[3] = {0.0, 0.0, 0.0};
+      for (int32_t t = ptr[r]; t < ptr[r + 1]; ++t) {
+        const int4 v4 = m.lnods[inc[t] >> 2];
+        if (v4.x != j && v4.y != j && v4.z != j && v4.w != j) continue;
+        const El el = element(t);
+        const int b = el.v[0] == j ? 0 : el.v[1] == j ? 1 : 2;
+        a += dot(el.w, el.c[b]);
+        g[0] += el.ci.x;
+        g[1] += el.ci.y;
+        g[2] += el.ci.z;
+      }
+      sa += a;
+      if constexpr (MODE == 0) {
+        Ao[q] = (Out)a;
+        for (int d = 0; d < 3; ++d) {
+          Go[d * m.nnz + q] = (Out)(-g[d] / 24.0);
+          sg[d] += g[d];
+        }
+      } else {
+        Ao[q] = (Out)((double)As[q] + a);
+      }
+    }
+    if (len > 0) {
+      if constexpr (MODE == 0) {
+        Ao[dpos] = (Out)(f.kmass * detsum - sa);
+        for (int d = 0; d < 3; ++d) Go[d * m.nnz + dpos] = (Out)(-sg[d] / 72.0);
+      } else {
+        Ao[dpos] = (Out)((double)As[dpos] - sa);
+      }
+    }
+  }
+  const V3<double> un = vel(f.un, i);
+  Out* Rh = static_cast<Out*>(rhs);
+  Rh[i] = (Out)(f.kmass * detsum * un.x);
+  Rh[m.n + i] = (Out)(f.kmass * detsum * un.y);
+  Rh[2 * m.n + i] = (Out)(f.kmass * detsum * un.z);
+  if constexpr (MODE == 2) {
+    static_cast<Out*>(dt_rho)[i] = (Out)(f.kmass * detsum);
+    static_cast<Out*>(mass_rho)[i] = (Out)(kmr * detsum);
   }
 }
 
@@ -2211,6 +2358,27 @@ static nsi_status fix_exact_rows(NsiHandle* h, const FieldView& f, int mode, voi
 
 // `rec` (nullptr: the handle's buffer) receives the row gather's per-call
 // node records
+// after any row-gather assembly or time step: the long rows (nothing if
+// there are none)
+template <int P>
+static nsi_status fix_long_rows(NsiHandle* h, const FieldView& f, int mode, const void* A_static, void* A, void* G,
+                                void* rhs, void* dt_rho, void* mass_rho, double kmr, cudaStream_t s) {
+  if (h->long_rows == 0) return NSI_OK;
+  const MeshView m = view_of(h);
+  const int blk = 64;
+  const int64_t grid = (h->long_rows + blk - 1) / blk;
+  if (mode == 0)
+    long_rows_kernel<P, 0><<<grid, blk, 0, s>>>(m, f, A_static, A, G, rhs, dt_rho, mass_rho, kmr, h->long_list,
+                                               h->long_ptr, h->long_inc, h->long_rows);
+  else if (mode == 1)
+    long_rows_kernel<P, 1><<<grid, blk, 0, s>>>(m, f, A_static, A, G, rhs, dt_rho, mass_rho, kmr, h->long_list,
+                                               h->long_ptr, h->long_inc, h->long_rows);
+  else
+    long_rows_kernel<P, 2><<<grid, blk, 0, s>>>(m, f, A_static, A, G, rhs, dt_rho, mass_rho, kmr, h->long_list,
+                                               h->long_ptr, h->long_inc, h->long_rows);
+  return check_launch("long_rows_kernel");
+}
+
 template <int P>
 static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s,
                                   void* rec = nullptr) {
@@ -2254,7 +2422,7 @@ static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutVie
     return NSI_OK;
   }
   // row gather
-  if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode needs rows of at most 32 entries");
+  if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "row-gather mode not available for this mesh");
   nsi_status st = h->debug ? set_gather_smem<P, true>() : set_gather_smem<P, false>();
   if (st) return st;
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
@@ -2267,7 +2435,7 @@ static nsi_status assemble_core_p(NsiHandle* h, const FieldView& f, const OutVie
     return check_launch("fan_kernel");
   }
   const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
+  const GatherSmem lay = gather_smem(P, R, h->plan.w, h->plan.max_block_entries, h->plan.max_block_steps);
   const size_t smem = lay.total();
   if (h->persistent) {
     int per_sm = 0, sms = 0, dev = 0;
@@ -2295,7 +2463,9 @@ template <int P>
 static nsi_status assemble_p(NsiHandle* h, const FieldView& f, const OutView& o, int mode, cudaStream_t s) {
   nsi_status st = assemble_core_p<P>(h, f, o, mode, s);
   if (st) return st;
-  return fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
+  st = fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
+  if (st || mode != NSI_SCATTER_GATHER) return st;
+  return fix_long_rows<P>(h, f, 0, nullptr, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
 }
 
 static nsi_status check_call(const NsiHandle* h, const NsiFields* f, const NsiOutputs* o) {
@@ -2354,7 +2524,7 @@ static nsi_status step_p(NsiHandle* h, const FieldView& f, const StepView& o, cu
   nsi_status st = h->debug ? set_step_smem<P, NODAL, true>() : set_step_smem<P, NODAL, false>();
   if (st) return st;
   const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps, true);
+  const GatherSmem lay = gather_smem(P, R, h->plan.w, h->plan.max_block_entries, h->plan.max_block_steps, true);
   const size_t smem = lay.total();
   if (smem > 200 * 1024) return fail(NSI_ERR_UNSUPPORTED, "the time-step layout needs more shared memory than a block has");
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, h->rec);
@@ -2383,12 +2553,14 @@ static nsi_status step_p(NsiHandle* h, const FieldView& f, const StepView& o, cu
     st = check_launch("step_kernel");
   }
   if (st) return st;
-  return fix_exact_rows<P>(h, f, NODAL ? 2 : 1, nullptr, nullptr, o.rhs, o.dt_rho, o.mass_rho, o.kmr, s);
+  st = fix_exact_rows<P>(h, f, NODAL ? 2 : 1, nullptr, nullptr, o.rhs, o.dt_rho, o.mass_rho, o.kmr, s);
+  if (st) return st;
+  return fix_long_rows<P>(h, f, NODAL ? 2 : 1, o.A_static, o.A, nullptr, o.rhs, o.dt_rho, o.mass_rho, o.kmr, s);
 }
 
 static nsi_status step_dispatch(NsiHandle* h, const NsiFields* f, const StepView& o, bool nodal, cudaStream_t s) {
   if (!h->gather_ok || h->n == 0)
-    return h->n == 0 ? NSI_OK : fail(NSI_ERR_UNSUPPORTED, "the time-step kernels need rows of at most 32 entries");
+    return h->n == 0 ? NSI_OK : fail(NSI_ERR_UNSUPPORTED, "the time-step kernels need the row-gather map");
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");
@@ -2411,9 +2583,13 @@ template <int P>
 static nsi_status batched_p(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os, int count,
                             cudaStream_t s) {
   nsi_status st = batched_core_p<P>(hs, fs, os, count, s);
-  for (int k = 0; k < count && !st; ++k)
+  for (int k = 0; k < count && !st; ++k) {
     st = fix_exact_rows<P>(hs[k], fields_of(&fs[k]), 0, os[k].A_val, os[k].G_val, os[k].rhs, nullptr, nullptr, 0.0,
                            s);
+    if (!st)
+      st = fix_long_rows<P>(hs[k], fields_of(&fs[k]), 0, nullptr, os[k].A_val, os[k].G_val, os[k].rhs, nullptr,
+                            nullptr, 0.0, s);
+  }
   return st;
 }
 
@@ -2475,7 +2651,7 @@ static nsi_status batched_core_p(NsiHandle* const* hs, const NsiFields* fs, cons
     const NsiHandle* h = hs[k];
     max_entries = std::max(max_entries, use[k]->max_block_entries);
     max_steps = std::max(max_steps, use[k]->max_block_steps);
-    max_row = std::max(max_row, h->max_row);
+    max_row = std::max(max_row, use[k]->w);
     args.item[k].m = view_of(h);
     args.item[k].f = fields_of(&fs[k]);
     args.item[k].o = OutView{os[k].A_val, os[k].G_val, os[k].rhs};
@@ -2567,7 +2743,9 @@ static nsi_status assemble_noalloc_p(NsiHandle* h, const FieldView& f, const Out
                                      cudaStream_t s) {
   nsi_status st = assemble_core_p<P>(h, f, o, NSI_SCATTER_GATHER, s, scratch);
   if (st) return st;
-  return fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
+  st = fix_exact_rows<P>(h, f, 0, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
+  if (st) return st;
+  return fix_long_rows<P>(h, f, 0, nullptr, o.A, o.G, o.rhs, nullptr, nullptr, 0.0, s);
 }
 
 }  // namespace nsi
@@ -2592,7 +2770,7 @@ static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOut
   const FieldView fv = fields_of(fd);
   const OutView ov{od->A_val, od->G_val, od->rhs};
   const int R = h->plan.rows_per_block;
-  const GatherSmem lay = gather_smem(P, R, h->max_row, h->plan.max_block_entries, h->plan.max_block_steps);
+  const GatherSmem lay = gather_smem(P, R, h->plan.w, h->plan.max_block_entries, h->plan.max_block_steps);
   const size_t smem = lay.total();
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, fv, h->rec);
   const int64_t nb = h->plan.n_blocks;
@@ -2712,7 +2890,7 @@ nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream)
 nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {
   nsi_status st = check_call(h, f, o);
   if (st) return st;
-  if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "the allocation-free call needs the row-gather mode (rows of at most 32 entries)");
+  if (!h->gather_ok) return fail(NSI_ERR_UNSUPPORTED, "the allocation-free call needs the row-gather mode");
   const size_t rec = h->precision == NSI_FP64 ? 64 : 32;
   if ((size_t)h->n * rec > NOALLOC_SCRATCH_BYTES) {
     char buf[200];
@@ -2838,7 +3016,8 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f, const NsiOutputs*
   }
   char* ob = base + ((u_bytes + 255) / 256) * 256;
   NsiOutputs od{ob, ob + osz * h->nnz, ob + osz * 4 * h->nnz};
-  if (resolve_mode(h, NSI_SCATTER_AUTO) == NSI_SCATTER_GATHER && !h->use_fan && h->n > 0 && h->exact_rows == 0) {
+  if (resolve_mode(h, NSI_SCATTER_AUTO) == NSI_SCATTER_GATHER && !h->use_fan && h->n > 0 && h->exact_rows == 0 &&
+      h->long_rows == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");

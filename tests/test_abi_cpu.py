@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version():
-    assert nsi.nsi_abi_version() == 1
+    assert nsi.nsi_abi_version() == 2
 
 
 def test_struct_layouts_match_header():
@@ -46,7 +46,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(nsi.NsiOptions) == 32
     assert ctypes.sizeof(nsi.NsiFields) == 72
     assert ctypes.sizeof(nsi.NsiOutputs) == 24
-    assert ctypes.sizeof(nsi.NsiInfo) == 64
+    assert ctypes.sizeof(nsi.NsiInfo) == 72
 
 
 def test_null_arguments_rejected_without_gpu():

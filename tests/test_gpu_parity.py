@@ -407,10 +407,10 @@ def _fan_mesh(m):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
 def test_longest_rows_of_the_row_gather(precision):
-    """Rows of 32 entries, the most the row gather takes (five bits of row
-    position per walk step), run on it and match the oracle, in the assembly
-    and the cached-geometry step; a 33-entry row makes the default mode fall
-    back to atomics (still matching) and an explicit row-gather request fail."""
+    """Rows of 32 entries, the most the row-gather kernels take (five bits of
+    row position per walk step), run on them and match the oracle, in the
+    assembly and the cached-geometry step; with 33-entry rows the mesh stays
+    on the row gather, the two long rows computed by the per-row kernel."""
     coord, lnods, u = _fan_mesh(30)
     asm = nsi.Assembler(coord, lnods, precision=precision)
     assert asm.max_row == 32 and asm.scatter == nsi.SCATTERS["gather"]
@@ -429,17 +429,19 @@ def test_longest_rows_of_the_row_gather(precision):
     assert max(err2.values()) <= TOL[precision], err2
     coord, lnods, u = _fan_mesh(31)
     asm = nsi.Assembler(coord, lnods, precision=precision)
-    assert asm.max_row == 33 and asm.scatter == nsi.SCATTERS["atomic"]
-    A, G, rhs = (x.double().cpu().numpy() for x in asm.assemble(torch.as_tensor(u.T.copy())))
+    assert asm.max_row == 33 and asm.scatter == nsi.SCATTERS["gather"] and asm.info().long_rows == 2
+    ut = torch.as_tensor(u.T.copy())
+    A, G, rhs = (x.double().cpu().numpy() for x in asm.assemble(ut))
+    A_static, _ = asm.static_part()
+    A2, rhs2 = (x.double().cpu().numpy() for x in asm.assemble_convective(ut, A_static))
+    At, Gt, rhst = (x.double().cpu().numpy() for x in asm.assemble(ut, scatter="atomic"))
     rp = asm.pattern()[0].cpu().numpy()
     asm.close()
     uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
     _, _, oA, oG, orhs = oracle.assemble(coord, lnods, uo, None, RHO, MU, DT)
-    err = errors(rp, A, G, rhs, oA, oG, orhs)
-    assert max(err.values()) <= TOL[precision], err
-    with pytest.raises(nsi.NsiError) as ex:
-        nsi.Assembler(coord, lnods, precision=precision, scatter="gather")
-    assert ex.value.status == nsi.NSI_ERR_UNSUPPORTED
+    for got in ((A, G, rhs), (A2, oG, rhs2), (At, Gt, rhst)):
+        err = errors(rp, *got, oA, oG, orhs)
+        assert max(err.values()) <= TOL[precision], err
 
 
 def _sliver_mesh():

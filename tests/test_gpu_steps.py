@@ -107,8 +107,11 @@ def test_nodal_outputs_match_oracle(precision, ci):
     asm.close()
 
 
-def test_steps_refuse_rows_beyond_the_walk():
-    """A node in more than 31 neighbours' elements has no walk: NSI_ERR_UNSUPPORTED."""
+def test_steps_take_rows_beyond_the_walk():
+    """Rows of more than 32 entries (a fan of 40 tets around an edge: rows of
+    42 entries at its two ends) no longer make the time-step kernels refuse the
+    mesh: those rows are computed by the per-row kernel.  Checked against the
+    oracle's assembly at u = 0 (A_static) plus the convection."""
     m = 40
     ang = 2 * np.pi * np.arange(m) / m
     coord = np.vstack([[0, 0, 0], np.c_[np.cos(ang), np.sin(ang), np.zeros(m)], [0, 0, 1]]).astype(float)
@@ -121,13 +124,18 @@ def test_steps_refuse_rows_beyond_the_walk():
             t[2], t[3] = t[3], t[2]
         lnods.append(t)
     lnods = np.array(lnods, dtype=np.int32)
+    u = np.random.default_rng(94).standard_normal(coord.shape)
     asm = nsi.Assembler(coord, lnods, precision="mixed64")
-    assert asm.max_row > 32
-    u = torch.zeros(3, coord.shape[0], dtype=torch.float32, device="cuda")
-    A_static = torch.zeros(asm.nnz, dtype=torch.float64, device="cuda")
-    with pytest.raises(nsi.NsiError) as e:
-        asm.assemble_convective(u, A_static)
-    assert e.value.status == nsi.NSI_ERR_UNSUPPORTED
+    assert asm.max_row == 42 and asm.info().long_rows == 2
+    ut = torch.as_tensor(u.T.copy())
+    A_static, _ = asm.static_part(rho=RHO, mu=MU, dt=DT)
+    A, rhs = (x.double().cpu().numpy() for x in asm.assemble_convective(ut, A_static, rho=RHO, mu=MU, dt=DT))
+    rp = asm.pattern()[0].cpu().numpy()
+    asm.close()
+    _, _, oA, oG, orhs = oracle.assemble(coord, lnods, vel_in(u, "mixed64"), None, RHO, MU, DT)
+    assert row_scaled_err(rp, A, oA) <= TOL["mixed64"]
+    for k in range(3):
+        assert vec_scaled_err(rhs[k], orhs[k]) <= TOL["mixed64"]
     with pytest.raises(nsi.NsiError):
         asm.nodal(u)
     asm.close()
