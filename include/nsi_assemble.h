@@ -289,6 +289,34 @@ nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOut
 nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream);
 
 /*
+ * The exchange step of one mesh assembled by several ranks, each on a
+ * disjoint set of its elements (paper Section III-C gives disjoint element
+ * sets to concurrent engines; splitting one mesh over GPUs this way is this
+ * library's design): each rank's assembly leaves partial sums in the rows of
+ * nodes on the partition interfaces, and the rank owning such a node adds
+ * the others' values into its row.  These two calls move and add values; the
+ * partition, the ownership and the index maps are the caller's
+ * (paper_2111_05651_gb300/partition.py builds them, and exchanges the
+ * buffers with torch.distributed).
+ *
+ * nsi_gather_values: dst[k * ncomp + c] = src[c][idx[k]] for k < count, c <
+ *   ncomp -- the values of the chosen entries of ncomp component arrays
+ *   (device pointers, e.g. A and the three G arrays), packed row-major into
+ *   the device buffer dst.
+ * nsi_add_values: dst[c][idx[k]] += src[k * ncomp + c] -- packed values added
+ *   into component arrays.  The idx of one call must be distinct (each
+ *   position is read and written by one thread); the order of the additions
+ *   is the order of the calls.
+ * src/dst: host arrays of ncomp device pointers (1 <= ncomp <= 4); idx: device
+ * int32 [count]; value_bytes: 8 (double) or 4 (float).  Enqueued on `stream`;
+ * no allocation.  count = 0 does nothing.
+ */
+nsi_status nsi_gather_values(const void* const* src, int32_t ncomp, const int32_t* idx, int64_t count, void* dst,
+                             int32_t value_bytes, void* stream);
+nsi_status nsi_add_values(void* const* dst, int32_t ncomp, const int32_t* idx, int64_t count, const void* src,
+                          int32_t value_bytes, void* stream);
+
+/*
  * Synchronise `stream` and read the handle's device error word: NSI_OK, or
  * NSI_ERR_DEVICE_CHECK (bounds check fired; the word is then cleared).
  */

@@ -103,6 +103,8 @@ _SIGNATURES = {
     "nsi_autotune": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), ctypes.c_int32, _P,
                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "nsi_set_launch": [_P, ctypes.c_int32, ctypes.c_int32],
+    "nsi_gather_values": [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int32, _P],
+    "nsi_add_values": [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int32, _P],
 }
 
 _lib = None
@@ -469,6 +471,41 @@ class Assembler:
             if not ev.cuda_event:  # torch creates the CUDA event on first record
                 ev.record()
         nsi_set_timing_events(self.handle, ctypes.c_void_p(start.cuda_event), ctypes.c_void_p(stop.cuda_event))
+
+
+def _components(first, rest, stride, ncomp):
+    """Device pointers of ncomp component arrays: ``first`` (or None) then the
+    rows of ``rest`` (a [k, stride] tensor)."""
+    ptrs = []
+    if first is not None:
+        ptrs.append(first.data_ptr())
+    es = rest.element_size()
+    while len(ptrs) < ncomp:
+        ptrs.append(rest.data_ptr() + (len(ptrs) - (first is not None)) * stride * es)
+    return (ctypes.c_void_p * ncomp)(*ptrs)
+
+
+def gather_values(first, rest, stride, idx, ncomp=4, stream=None):
+    """[count, ncomp] tensor of the values at positions idx of the component
+    arrays (first, rest[0], rest[1], ...) -- e.g. A and G -- via nsi_gather_values."""
+    torch = _torch()
+    count = int(idx.numel())
+    dst = torch.empty((count, ncomp), dtype=rest.dtype, device=rest.device)
+    comps = _components(first, rest, stride, ncomp)
+    _check(load_library().nsi_gather_values(comps, ncomp, _ptr(idx), count, _ptr(dst), rest.element_size(),
+                                            _stream_ptr(stream)))
+    return dst
+
+
+def add_values(first, rest, stride, idx, vals, ncomp=4, stream=None):
+    """(first, rest[0], ...)[idx[k]] += vals[k, :] via nsi_add_values (idx distinct)."""
+    count = int(idx.numel())
+    if count == 0:
+        return
+    comps = _components(first, rest, stride, ncomp)
+    vals = vals.contiguous()
+    _check(load_library().nsi_add_values(comps, ncomp, _ptr(idx), count, _ptr(vals), rest.element_size(),
+                                         _stream_ptr(stream)))
 
 
 def assemble_batched(assemblers, us, rho=1.0, mu=1e-3, dt=1e-2, outs=None, stream=None):

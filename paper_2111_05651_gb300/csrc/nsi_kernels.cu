@@ -2299,6 +2299,33 @@ __global__ void __launch_bounds__(256) residual_kernel(MeshView m, FieldView f, 
   }
 }
 
+// --------------------------------------------- partition exchange ---
+// The interface-row sum of a mesh split over ranks (disjoint element sets):
+// values of chosen entries packed into an exchange buffer, and received
+// values added into the owner's rows.
+constexpr int XCH_MAX_COMP = 4;
+struct CompPtrs {
+  void* p[XCH_MAX_COMP];
+};
+// dst[k][c] = comp[c][idx[k]] (dst row-major [count][ncomp])
+template <typename V>
+__global__ void __launch_bounds__(256) gather_values_kernel(CompPtrs src, int ncomp, const int32_t* __restrict__ idx,
+                                                            int64_t count, V* __restrict__ dst) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int32_t i = idx[k];
+  for (int c = 0; c < ncomp; ++c) dst[k * ncomp + c] = static_cast<const V*>(src.p[c])[i];
+}
+// comp[c][idx[k]] += src[k][c]; the positions of one call are distinct
+template <typename V>
+__global__ void __launch_bounds__(256) add_values_kernel(CompPtrs dst, int ncomp, const int32_t* __restrict__ idx,
+                                                         int64_t count, const V* __restrict__ src) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int32_t i = idx[k];
+  for (int c = 0; c < ncomp; ++c) static_cast<V*>(dst.p[c])[i] += src[k * ncomp + c];
+}
+
 // ----------------------------------------------------------- launchers ---
 static nsi_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -2885,6 +2912,44 @@ nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->precision == NSI_FP64) return residual_p<NSI_FP64>(h, fv, r, s);
   return residual_p<NSI_MIXED_F32_ACC32>(h, fv, r, s);
+}
+
+static nsi_status values_args(void* const* comp, int32_t ncomp, const int32_t* idx, int64_t count, const void* buf,
+                              int32_t value_bytes, CompPtrs& cp) {
+  if (count < 0) return fail(NSI_ERR_INVALID_ARG, "count < 0");
+  if (ncomp < 1 || ncomp > XCH_MAX_COMP) return fail(NSI_ERR_INVALID_ARG, "ncomp must be in [1, 4]");
+  if (value_bytes != 4 && value_bytes != 8) return fail(NSI_ERR_INVALID_ARG, "value_bytes must be 4 or 8");
+  if (count > 0 && (!comp || !idx || !buf)) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
+  for (int c = 0; c < XCH_MAX_COMP; ++c) cp.p[c] = nullptr;
+  for (int c = 0; c < ncomp && count > 0; ++c) {
+    if (!comp[c]) return fail(NSI_ERR_INVALID_ARG, "NULL component pointer");
+    cp.p[c] = comp[c];
+  }
+  return NSI_OK;
+}
+
+nsi_status nsi_gather_values(const void* const* src, int32_t ncomp, const int32_t* idx, int64_t count, void* dst,
+                             int32_t value_bytes, void* stream) {
+  CompPtrs cp;
+  nsi_status st = values_args(const_cast<void* const*>(src), ncomp, idx, count, dst, value_bytes, cp);
+  if (st || count == 0) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t grid = (count + 255) / 256;
+  if (value_bytes == 8) gather_values_kernel<double><<<grid, 256, 0, s>>>(cp, ncomp, idx, count, static_cast<double*>(dst));
+  else gather_values_kernel<float><<<grid, 256, 0, s>>>(cp, ncomp, idx, count, static_cast<float*>(dst));
+  return check_launch("gather_values_kernel");
+}
+
+nsi_status nsi_add_values(void* const* dst, int32_t ncomp, const int32_t* idx, int64_t count, const void* src,
+                          int32_t value_bytes, void* stream) {
+  CompPtrs cp;
+  nsi_status st = values_args(dst, ncomp, idx, count, src, value_bytes, cp);
+  if (st || count == 0) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t grid = (count + 255) / 256;
+  if (value_bytes == 8) add_values_kernel<double><<<grid, 256, 0, s>>>(cp, ncomp, idx, count, static_cast<const double*>(src));
+  else add_values_kernel<float><<<grid, 256, 0, s>>>(cp, ncomp, idx, count, static_cast<const float*>(src));
+  return check_launch("add_values_kernel");
 }
 
 nsi_status nsi_assemble_noalloc(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {
