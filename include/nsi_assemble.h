@@ -42,8 +42,13 @@
  *      NSI_MIXED_F32_ACC64 u, u_n: float;   A, G, rhs: double.  Gathers and
  *                          element arithmetic in float (coordinates kept as
  *                          float hi/lo pairs so edge vectors keep ~48 bits);
- *                          sums accumulated as compensated float pairs
- *                          (about 48 significant bits) and stored as double.
+ *                          A, the lumped mass and the RHS accumulated as
+ *                          compensated float pairs (about 48 significant
+ *                          bits; A's diagonal is the mass minus its row's
+ *                          other entries), G in float (its element terms are
+ *                          float products; about 1e-7 of the row's largest
+ *                          entry); stored as double.  The element-centric
+ *                          modes (colour, atomic) add in double.
  *      NSI_MIXED_F32_ACC32 u, u_n: float;   A, G, rhs: float.
  *  - Outputs are OVERWRITTEN by every assemble call (the call defines every
  *    entry; no prior zeroing is needed).
@@ -134,16 +139,23 @@ typedef struct {
  * colouring and packed coordinate copies.  Synchronous; allocates device
  * memory owned by the handle.  `stream` (a cudaStream_t, may be NULL) is used
  * for the uploads.  On failure *out is NULL.
+ * Paper: the CSR pattern is where perform_assembly_in_global_system (Listing
+ * 2, Section II-A) adds the element matrices; the paper's kernel receives the
+ * mesh once and assembles every time step (Section II), so the pattern and
+ * the gather maps are built once per mesh here.
  */
 nsi_status nsi_assemble_create(const NsiMesh* mesh, const NsiOptions* opts, void* stream,
                                NsiHandle** out);
 
-/* Release a handle (NULL is allowed).  Synchronises the device first. */
+/* Release a handle (NULL is allowed).  Synchronises the device first.
+ * (No counterpart in the paper: resource management of this library.) */
 nsi_status nsi_assemble_destroy(NsiHandle* h);
 
 /*
  * The handle's CSR pattern (device pointers owned by the handle, valid until
  * destroy) and its sizes.  Any output pointer may be NULL.
+ * (No counterpart in the paper: the pattern of the global matrix of
+ * Section II-A, exposed to the caller.)
  */
 nsi_status nsi_csr_pattern(const NsiHandle* h, const int32_t** row_ptr, const int32_t** col_idx,
                            int64_t* nnz);
@@ -151,11 +163,13 @@ nsi_status nsi_csr_pattern(const NsiHandle* h, const int32_t** row_ptr, const in
 /*
  * Copy the handle's CSR pattern into caller buffers (host or device;
  * row_ptr: n_nodes + 1 entries, col_idx: nnz entries; either may be NULL).
- * Enqueued on `stream`, which is then synchronised.
+ * Enqueued on `stream`, which is then synchronised.  (No counterpart in the
+ * paper; as nsi_csr_pattern.)
  */
 nsi_status nsi_csr_pattern_copy(const NsiHandle* h, int32_t* row_ptr, int32_t* col_idx, void* stream);
 
-/* Sizes and facts about the handle: nodes, elements, nnz, colours, max row length. */
+/* Sizes and facts about the handle: nodes, elements, nnz, colours, max row
+ * length, launch choices.  (No counterpart in the paper.) */
 typedef struct {
     int64_t n_nodes, n_elems, nnz;
     int32_t n_colors, max_row, precision, scatter;
@@ -186,7 +200,10 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
  */
 nsi_status nsi_assemble(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream);
 
-/* Same as nsi_assemble with an explicit scatter mode (nsi_scatter). */
+/* Same as nsi_assemble with an explicit scatter mode (nsi_scatter).  Paper:
+ * the scatter of Listing 2 (perform_assembly_in_global_system), whose
+ * conflicts shaped the FPGA design (Section III-B); the modes are this
+ * library's ways of doing it on a GPU. */
 nsi_status nsi_assemble_mode(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t scatter,
                              void* stream);
 
@@ -195,6 +212,8 @@ nsi_status nsi_assemble_mode(NsiHandle* h, const NsiFields* f, const NsiOutputs*
  * strides over every mesh's rows).  All handles must share one precision and
  * support the row-gather mode; count <= NSI_MAX_BATCH.  Pointers are passed to
  * the kernel by value, so the call is graph-capturable and allocates nothing.
+ * (No counterpart in the paper, which assembles one mesh per call; the
+ * per-mesh operation is nsi_assemble's.)
  */
 #define NSI_MAX_BATCH 128
 nsi_status nsi_assemble_batched(NsiHandle* const* hs, const NsiFields* fs, const NsiOutputs* os,
@@ -238,7 +257,8 @@ nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void*
  * grad_mu = sum_{i,k} w[k][i] dR[k][i]/dmu.  Element geometry is recomputed
  * (no element matrices are stored).  w, grad_u: device [3][n_nodes] in the
  * handle's velocity type; grad_mu: device double scalar.  Both outputs are
- * overwritten.
+ * overwritten.  (No counterpart in the paper: the derivative of the
+ * Section II-A assembly with respect to the velocity and the viscosity.)
  */
 nsi_status nsi_assemble_vjp(NsiHandle* h, const NsiFields* f, const void* w, void* grad_u,
                             double* grad_mu, void* stream);
@@ -247,7 +267,8 @@ nsi_status nsi_assemble_vjp(NsiHandle* h, const NsiFields* f, const void* w, voi
  * Residual of the assembled system without forming the matrix:
  * R[k][i] = sum_j A_ij u[k][j] - rhs[k][i] for the velocities in `f` (the
  * quantity whose adjoint nsi_assemble_vjp computes).  r: device [3][n_nodes]
- * in the handle's velocity type, overwritten.
+ * in the handle's velocity type, overwritten.  (No counterpart in the
+ * paper.)
  */
 nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream);
 
@@ -256,7 +277,9 @@ nsi_status nsi_residual(NsiHandle* h, const NsiFields* f, void* r, void* stream)
  * host memory to handle-owned device staging, assembles, and copies A, G, rhs
  * back to the host buffers in `o` (pinned memory recommended), all on
  * `stream`, then synchronises it.  The first call allocates the staging
- * buffers; later calls reuse them.
+ * buffers; later calls reuse them.  Paper: the host-side movement of the
+ * FPGA designs (Section III-B/C: the host streams element data to the card
+ * and receives results over PCIe) has this call as its counterpart here.
  */
 nsi_status nsi_assemble_host(NsiHandle* h, const NsiFields* f_host, const NsiOutputs* o_host,
                              void* stream);
@@ -319,6 +342,7 @@ nsi_status nsi_add_values(void* const* dst, int32_t ncomp, const int32_t* idx, i
 /*
  * Synchronise `stream` and read the handle's device error word: NSI_OK, or
  * NSI_ERR_DEVICE_CHECK (bounds check fired; the word is then cleared).
+ * (No counterpart in the paper.)
  */
 nsi_status nsi_device_status(NsiHandle* h, void* stream);
 
@@ -331,6 +355,8 @@ nsi_status nsi_device_status(NsiHandle* h, void* stream);
  * warm-up call, keeps the fastest as the handle's default, and reports it
  * (chosen_rows as in nsi_set_launch; 0 for colouring).
  * Synchronises `stream`; overwrites the outputs.  Either output may be NULL.
+ * (No counterpart in the paper, whose FPGA designs were tuned by hand,
+ * Section III.)
  */
 nsi_status nsi_autotune(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, int32_t reps, void* stream,
                         int32_t* chosen_scatter, int32_t* chosen_rows);
@@ -353,13 +379,15 @@ nsi_status nsi_set_launch(NsiHandle* h, int32_t scatter, int32_t rows_per_block)
  * before its main assembly kernel and `stop` right after it, on the call's
  * stream, so that the caller can time that kernel alone (the per-call node
  * packing and output zeroing stay outside the pair).  Pass NULLs to disable.
+ * (No counterpart in the paper.)
  */
 nsi_status nsi_set_timing_events(NsiHandle* h, void* start, void* stop);
 
-/* Message describing the last failure on the calling thread ("" if none). */
+/* Message describing the last failure on the calling thread ("" if none).
+ * (No counterpart in the paper.) */
 const char* nsi_last_error(void);
 
-/* NSI_ABI_VERSION of the loaded library. */
+/* NSI_ABI_VERSION of the loaded library.  (No counterpart in the paper.) */
 int32_t nsi_abi_version(void);
 
 #ifdef __cplusplus
