@@ -176,8 +176,8 @@ def assemble_rows(coord, lnods, u, rows, un=None, rho=1.0, mu=1e-3, dt=1e-2, max
 
 
 def nodal(coord, lnods, un, rho=1.0, dt=1e-2):
-    """Nodal outputs of the paper's assembly (perform_assembly_in_global_system,
-    Listing 2): (rhsid [3, n], dt_rho [n], mass_rho [n]); see ``oracle_nodal``."""
+    """The paper's per-node outputs of the assembly (Section II-A): (rhsid
+    [3, n], dt_rho [n], mass_rho [n]); see ``oracle_nodal``."""
     lib = _load()
     coord, lnods, un = _f64(coord), _ln(lnods), _f64(un)
     n = coord.shape[0]

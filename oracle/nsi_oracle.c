@@ -6,38 +6,29 @@
  * the CPU-baseline leg of the benchmark may load it; the library never does.
  * It shares no code, header, table or constant with the CUDA path.
  *
- * What is computed (Section II-A, Listings 1 and 2 of the paper; the per-term
- * formulas are the Galerkin P1 form, since the paper names the subroutines
- * but not their equations):
+ * What is computed: the element matrix assembly of Section II-A of the paper
+ * for linear tetrahedra (4 nodes, 3 dimensions), in the Galerkin P1 form
+ * (the paper names the terms but prints no formulas).  For an element with
+ * nodes a = 0..3, shape functions N_a and velocity u_h = sum_c N_c u_c:
  *
- *   per linear tetrahedron e with nodes lnods[e][0..3] (4 nodes, 3 dims):
- *     gather      elcod[a][i] = coord[lnods[e][a]][i], elvel likewise
- *                 (calculate_transients, Listing 2)
- *     Jacobian    J[i][j] = d x_i / d xi_j = sum_a elcod[a][i] dN_a/dxi_j
- *                 det J, J^{-1} by cofactors, gpcar[a][i] = dN_a/dx_i
- *                 = sum_j Jinv[j][i] dN_a/dxi_j, gpvol[g] = w_g det J
- *                 (calculate_cartesian_derivatives, Listing 1)
- *     Gauss pts   4-point rule, barycentric (alpha, beta, beta, beta) and its
- *                 permutations, reference weight 1/24 each; beta=(5-sqrt 5)/20,
- *                 alpha = 1 - 3 beta (the printed 10-digit constants rounded)
- *     gp values   gpvel[g][k] = sum_c N_c(xi_g) elvel[c][k]
- *                 (calculate_gauss_point_values)
- *     matrices    agrau[g][b] = gpvel[g] . gpcar[b]; wgrgr[a][b] = gpcar[a].gpcar[b]
- *                 (calculate_element_matricies)
- *     A_e[a][b]   = sum_g gpvol[g] ( rho N_a(xi_g) agrau[g][b] + mu wgrgr[a][b] )
- *                   + delta_ab rho/dt sum_g gpvol[g] N_a(xi_g)   (row-sum lumped mass)
- *                 (calculate_convective_term_and_RHS, calculate_viscous_term)
- *     G_e[a][b][d]= - sum_g gpvol[g] gpcar[a][d] N_b(xi_g)
- *     b_e[a][k]   = rho/dt (sum_g gpvol[g] N_a(xi_g)) un[a][k]   (lumped RHS)
- *   assembly      A[row lnods[a], col lnods[b]] += A_e[a][b], G likewise on
- *                 the same CSR pattern, rhs[k][lnods[a]] += b_e[a][k]
- *                 (perform_assembly_in_global_system, Listing 2; here into a
- *                 CSR matrix), contributions added in increasing element order.
+ *   A_e[a][b]    = int rho N_a (u_h . grad N_b) + mu grad N_a . grad N_b      (convection, viscosity)
+ *                  + delta_ab rho/dt int N_a                                  (row-sum lumped mass)
+ *   G_e[a][b][d] = - int d_d N_a N_b                                          (pressure gradient)
+ *   b_e[a][k]    = rho/dt (int N_a) u^n_a[k]                                  (lumped right-hand side)
  *
- * Layouts: coord/u/un/w are node-major [n][3] (the paper's coord(3,npoin) with
- * the dimension fastest); lnods is [E][4], 0-based; CSR row_ptr[n+1],
- * col_idx[nnz] ascending per row, diagonal included; G is component-major
- * [3][nnz]; rhs is [3][n].
+ * The integrals are evaluated by the 4-point rule on the reference
+ * tetrahedron (barycentric points (alpha, beta, beta, beta) and its
+ * permutations, weights 1/24 of the reference volume 1/6 each, beta =
+ * (5 - sqrt 5)/20, alpha = 1 - 3 beta: the printed 10-digit constants are
+ * these rounded), exact for the degree-2 integrands above; the shape-function
+ * gradients are J^{-T} times the reference gradients, with the Jacobian J of
+ * the element map, its determinant and its inverse by cofactors.  The
+ * element matrices are summed over elements, in increasing element order,
+ * into a CSR matrix whose pattern is every node pair sharing an element.
+ *
+ * Layouts: coord/u/un/w are node-major [n][3] (the dimension fastest); lnods
+ * is [E][4], 0-based; CSR row_ptr[n+1], col_idx[nnz] ascending per row,
+ * diagonal included; G is component-major [3][nnz]; rhs is [3][n].
  *
  * All arithmetic is IEEE double (the paper: all calculations are double
  * precision, Section II-A).  Return codes: 0 ok, negative on bad input.
@@ -54,32 +45,34 @@
 #define PGAUS 4
 #define NDIME 3
 
-/* reference-element shape derivatives dN_a/dxi_j: N_0 = 1-xi-eta-zeta, N_j = xi_j */
-static const double DERIV[PNODE][NDIME] = {
+/* gradients of the reference shape functions N_0 = 1-xi-eta-zeta, N_j = xi_j */
+static const double REF_GRAD[PNODE][NDIME] = {
     {-1.0, -1.0, -1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
 
-/* shape function values N_c(xi_g) at the 4 Gauss points (barycentric coordinates) */
-static void gauss_rule(double shape[PGAUS][PNODE], double weight[PGAUS]) {
+/* the 4-point rule: N_c at point q (the barycentric coordinates of the point)
+   and the reference weights */
+static void quadrature_rule(double lam[PGAUS][PNODE], double wref[PGAUS]) {
     const double beta = (5.0 - sqrt(5.0)) / 20.0;
     const double alpha = 1.0 - 3.0 * beta;
-    for (int g = 0; g < PGAUS; ++g) {
-        for (int c = 0; c < PNODE; ++c) shape[g][c] = (c == g) ? alpha : beta;
-        weight[g] = 1.0 / 24.0; /* reference tet volume 1/6 split over 4 points */
+    for (int q = 0; q < PGAUS; ++q) {
+        for (int c = 0; c < PNODE; ++c) lam[q][c] = (c == q) ? alpha : beta;
+        wref[q] = 1.0 / 24.0; /* reference tet volume 1/6 split over 4 points */
     }
 }
 
 /*
- * Jacobian J[i][j] = dx_i/dxi_j, its determinant and inverse (by cofactors),
- * and the Cartesian shape derivatives gpcar[a][i] = dN_a/dx_i = sum_j
- * Jinv[j][i] dN_a/dxi_j (calculate_cartesian_derivatives, Listing 1).
+ * Shape-function gradients of a linear tetrahedron: the Jacobian
+ * J[i][j] = dx_i/dxi_j of the element map, its determinant, its inverse by
+ * cofactors, and grad[a][i] = dN_a/dx_i = sum_j Jinv[j][i] dN_a/dxi_j
+ * (Section II-A: Jacobian, determinant, inverse and Cartesian derivatives).
  * Returns det J.
  */
-static double cartesian_derivatives(const double X[PNODE][NDIME], double gpcar[PNODE][NDIME]) {
+static double shape_gradients(const double X[PNODE][NDIME], double grad[PNODE][NDIME]) {
     double J[NDIME][NDIME];
     for (int i = 0; i < NDIME; ++i)
         for (int j = 0; j < NDIME; ++j) {
             J[i][j] = 0.0;
-            for (int a = 0; a < PNODE; ++a) J[i][j] += X[a][i] * DERIV[a][j];
+            for (int a = 0; a < PNODE; ++a) J[i][j] += X[a][i] * REF_GRAD[a][j];
         }
     /* cofactor matrix C[i][j] = (-1)^{i+j} minor(i, j) */
     double C[NDIME][NDIME];
@@ -99,69 +92,71 @@ static double cartesian_derivatives(const double X[PNODE][NDIME], double gpcar[P
         for (int j = 0; j < NDIME; ++j) Jinv[i][j] = C[j][i] / det;
     for (int a = 0; a < PNODE; ++a)
         for (int i = 0; i < NDIME; ++i) {
-            gpcar[a][i] = 0.0;
-            for (int j = 0; j < NDIME; ++j) gpcar[a][i] += Jinv[j][i] * DERIV[a][j];
+            grad[a][i] = 0.0;
+            for (int j = 0; j < NDIME; ++j) grad[a][i] += Jinv[j][i] * REF_GRAD[a][j];
         }
     return det;
 }
 
 /*
- * Element matrices for one tetrahedron (Listing 1 subroutines, in order).
- * X: node coordinates, U: advection velocity, Un: velocity used by the RHS.
- * Returns det J (negative or zero for an inverted/degenerate element).
+ * The element integrals of the form above for one tetrahedron, by the
+ * 4-point rule.  X: node coordinates, U: advection velocity, Un: velocity of
+ * the right-hand side.  Returns det J (negative or zero for an inverted or
+ * degenerate element); *volume gets the element's volume.
  */
 double oracle_element(const double X[PNODE][NDIME], const double U[PNODE][NDIME],
                       const double Un[PNODE][NDIME], double rho, double mu, double dt,
                       double A[PNODE][PNODE], double G[PNODE][PNODE][NDIME],
                       double b[PNODE][NDIME], double* volume) {
-    double shape[PGAUS][PNODE], weight[PGAUS];
-    gauss_rule(shape, weight);
+    double lam[PGAUS][PNODE], wref[PGAUS];
+    quadrature_rule(lam, wref);
 
-    double gpcar[PGAUS][PNODE][NDIME], gpvol[PGAUS], detjac = 0.0;
-    /* calculate_cartesian_derivatives: loop over Gauss points (constant for P1) */
-    for (int g = 0; g < PGAUS; ++g) {
-        detjac = cartesian_derivatives(X, gpcar[g]);
-        gpvol[g] = weight[g] * detjac;
+    /* gradients and integration weights w_q det J at every point (the
+       gradients of a linear element are the same at every point) */
+    double grad[PGAUS][PNODE][NDIME], wq[PGAUS], detjac = 0.0;
+    for (int q = 0; q < PGAUS; ++q) {
+        detjac = shape_gradients(X, grad[q]);
+        wq[q] = wref[q] * detjac;
     }
 
-    /* calculate_gauss_point_values: advection velocity at each Gauss point */
-    double gpvel[PGAUS][NDIME];
-    for (int g = 0; g < PGAUS; ++g)
+    /* the advection velocity u_h at every point */
+    double uq[PGAUS][NDIME];
+    for (int q = 0; q < PGAUS; ++q)
         for (int k = 0; k < NDIME; ++k) {
-            gpvel[g][k] = 0.0;
-            for (int c = 0; c < PNODE; ++c) gpvel[g][k] += shape[g][c] * U[c][k];
+            uq[q][k] = 0.0;
+            for (int c = 0; c < PNODE; ++c) uq[q][k] += lam[q][c] * U[c][k];
         }
 
     memset(A, 0, sizeof(double) * PNODE * PNODE);
     memset(G, 0, sizeof(double) * PNODE * PNODE * NDIME);
     memset(b, 0, sizeof(double) * PNODE * NDIME);
     double vol = 0.0;
-    for (int g = 0; g < PGAUS; ++g) {
-        /* calculate_element_matricies */
-        double agrau[PNODE], wgrgr[PNODE][PNODE];
+    for (int q = 0; q < PGAUS; ++q) {
+        /* u_h . grad N_b and grad N_a . grad N_b at the point */
+        double adv[PNODE], stiff[PNODE][PNODE];
         for (int bb = 0; bb < PNODE; ++bb) {
-            agrau[bb] = 0.0;
-            for (int k = 0; k < NDIME; ++k) agrau[bb] += gpvel[g][k] * gpcar[g][bb][k];
+            adv[bb] = 0.0;
+            for (int k = 0; k < NDIME; ++k) adv[bb] += uq[q][k] * grad[q][bb][k];
         }
         for (int a = 0; a < PNODE; ++a)
             for (int bb = 0; bb < PNODE; ++bb) {
-                wgrgr[a][bb] = 0.0;
-                for (int k = 0; k < NDIME; ++k) wgrgr[a][bb] += gpcar[g][a][k] * gpcar[g][bb][k];
+                stiff[a][bb] = 0.0;
+                for (int k = 0; k < NDIME; ++k) stiff[a][bb] += grad[q][a][k] * grad[q][bb][k];
             }
-        /* convective + viscous terms */
+        /* convection rho N_a (u_h . grad N_b) and viscosity mu grad N_a . grad N_b */
         for (int a = 0; a < PNODE; ++a)
             for (int bb = 0; bb < PNODE; ++bb)
-                A[a][bb] += gpvol[g] * (rho * shape[g][a] * agrau[bb] + mu * wgrgr[a][bb]);
-        /* pressure-gradient block */
+                A[a][bb] += wq[q] * (rho * lam[q][a] * adv[bb] + mu * stiff[a][bb]);
+        /* pressure gradient -d_d N_a N_b */
         for (int a = 0; a < PNODE; ++a)
             for (int bb = 0; bb < PNODE; ++bb)
-                for (int d = 0; d < NDIME; ++d) G[a][bb][d] -= gpvol[g] * gpcar[g][a][d] * shape[g][bb];
-        vol += gpvol[g];
+                for (int d = 0; d < NDIME; ++d) G[a][bb][d] -= wq[q] * grad[q][a][d] * lam[q][bb];
+        vol += wq[q];
     }
-    /* row-sum lumped mass on the diagonal and lumped RHS */
+    /* row-sum lumped mass int N_a on the diagonal and in the right-hand side */
     for (int a = 0; a < PNODE; ++a) {
         double lump = 0.0;
-        for (int g = 0; g < PGAUS; ++g) lump += gpvol[g] * shape[g][a];
+        for (int q = 0; q < PGAUS; ++q) lump += wq[q] * lam[q][a];
         A[a][a] += rho * lump / dt;
         for (int k = 0; k < NDIME; ++k) b[a][k] = rho * lump * Un[a][k] / dt;
     }
@@ -169,9 +164,9 @@ double oracle_element(const double X[PNODE][NDIME], const double U[PNODE][NDIME]
     return detjac;
 }
 
-static void gather(const double* coord, const double* u, const double* un, const int32_t* ln,
-                   double X[PNODE][NDIME], double U[PNODE][NDIME], double Un[PNODE][NDIME]) {
-    /* calculate_transients (Listing 2) */
+/* the element's node coordinates and velocities, from the global arrays */
+static void element_nodes(const double* coord, const double* u, const double* un, const int32_t* ln,
+                          double X[PNODE][NDIME], double U[PNODE][NDIME], double Un[PNODE][NDIME]) {
     for (int a = 0; a < PNODE; ++a) {
         int64_t p = ln[a];
         for (int k = 0; k < NDIME; ++k) {
@@ -191,7 +186,7 @@ int oracle_element_batch(int64_t n, const double* coord, const int32_t* lnods, c
         for (int a = 0; a < PNODE; ++a)
             if (ln[a] < 0 || ln[a] >= n) return -1;
         double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
-        gather(coord, u, un, ln, X, U, Un);
+        element_nodes(coord, u, un, ln, X, U, Un);
         det[t] = oracle_element(X, U, Un, rho, mu, dt, (double(*)[PNODE])(A + 16 * t),
                                 (double(*)[PNODE][NDIME])(G + 48 * t), (double(*)[NDIME])(b + 12 * t),
                                 vol + t);
@@ -200,21 +195,21 @@ int oracle_element_batch(int64_t n, const double* coord, const int32_t* lnods, c
 }
 
 /*
- * Nodal outputs of perform_assembly_in_global_system (Listing 2), the paper's
- * own kernel outputs: for every element, in increasing element order, and
- * every node a of it,
- *   rhsid[k][lnods[a]]  += elrbu[k][a]   = rho/dt (sum_g gpvol[g] N_a(xi_g)) un[a][k]
- *   dt_rho[lnods[a]]    += eldtrho[a]    = rho/dt  sum_g gpvol[g] N_a(xi_g)
- *   mass_rho[lnods[a]]  += elmurho[a]    = rho     sum_g gpvol[g] N_a(xi_g)
- * The paper prints the accumulation, not the element values: eldtrho and
- * elmurho are read as the row-sum lumped density mass over dt and the lumped
- * density mass (the same lumping as the matrix diagonal and the RHS).
- * rhs is [3][n]; dt_rho and mass_rho are [n].
+ * The paper's per-node outputs of the assembly (Section II-A: the
+ * right-hand side rhsid and the nodal arrays dt_rho_nsi and mass_rho_nsi,
+ * accumulated over the elements of each node), in increasing element order:
+ *   rhsid[k][i]  += rho/dt (int_e N_a) un[a][k]
+ *   dt_rho[i]    += rho/dt  int_e N_a
+ *   mass_rho[i]  += rho     int_e N_a            for every element e and node a of it, i = lnods[e][a],
+ * with int_e N_a by the 4-point rule.  The paper gives the accumulation, not
+ * the element values: they are read as the row-sum lumped density mass over
+ * dt and the lumped density mass (the lumping of the matrix diagonal and the
+ * RHS).  rhs is [3][n]; dt_rho and mass_rho are [n].
  */
 int oracle_nodal(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* un,
                  double rho, double dt, double* rhs, double* dt_rho, double* mass_rho) {
-    double shape[PGAUS][PNODE], weight[PGAUS];
-    gauss_rule(shape, weight);
+    double lam[PGAUS][PNODE], wref[PGAUS];
+    quadrature_rule(lam, wref);
     memset(rhs, 0, sizeof(double) * 3 * n);
     memset(dt_rho, 0, sizeof(double) * n);
     memset(mass_rho, 0, sizeof(double) * n);
@@ -223,17 +218,17 @@ int oracle_nodal(int64_t n, int64_t E, const double* coord, const int32_t* lnods
         for (int a = 0; a < PNODE; ++a)
             if (ln[a] < 0 || ln[a] >= n) return -1;
         double X[PNODE][NDIME], Un[PNODE][NDIME];
-        gather(coord, un, un, ln, X, Un, Un);
-        double gpcar[PNODE][NDIME];
-        const double detjac = cartesian_derivatives(X, gpcar);
+        element_nodes(coord, un, un, ln, X, Un, Un);
+        double grad[PNODE][NDIME];
+        const double detjac = shape_gradients(X, grad);
         if (!(detjac > 0.0)) return -2;
         for (int a = 0; a < PNODE; ++a) {
             double lump = 0.0;
-            for (int g = 0; g < PGAUS; ++g) lump += weight[g] * detjac * shape[g][a];
-            const double eldtrho = rho * lump / dt, elmurho = rho * lump;
+            for (int g = 0; g < PGAUS; ++g) lump += wref[g] * detjac * lam[g][a];
+            const double mdt = rho * lump / dt, mrho = rho * lump;
             for (int k = 0; k < NDIME; ++k) rhs[k * n + ln[a]] += rho * lump * Un[a][k] / dt;
-            dt_rho[ln[a]] += eldtrho;
-            mass_rho[ln[a]] += elmurho;
+            dt_rho[ln[a]] += mdt;
+            mass_rho[ln[a]] += mrho;
         }
     }
     return 0;
@@ -305,9 +300,9 @@ int oracle_assemble(int64_t n, int64_t E, const double* coord, const int32_t* ln
             if (ln[a] < 0 || ln[a] >= n) return -1;
         double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
         double Ae[PNODE][PNODE], Ge[PNODE][PNODE][NDIME], be[PNODE][NDIME], vol;
-        gather(coord, u, un, ln, X, U, Un);
+        element_nodes(coord, u, un, ln, X, U, Un);
         oracle_element(X, U, Un, rho, mu, dt, Ae, Ge, be, &vol);
-        /* perform_assembly_in_global_system */
+        /* the element's 16 entries added at their CSR positions */
         for (int a = 0; a < PNODE; ++a) {
             for (int c = 0; c < PNODE; ++c) {
                 int64_t pos = find_pos(row_ptr, col_idx, ln[a], ln[c]);
@@ -353,7 +348,7 @@ int oracle_assemble_rows(int64_t n, int64_t E, const double* coord, const int32_
         if (!hit) continue;
         double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
         double Ae[PNODE][PNODE], Ge[PNODE][PNODE][NDIME], be[PNODE][NDIME], vol;
-        gather(coord, u, un, ln, X, U, Un);
+        element_nodes(coord, u, un, ln, X, U, Un);
         oracle_element(X, U, Un, rho, mu, dt, Ae, Ge, be, &vol);
         for (int a = 0; a < PNODE; ++a) {
             int64_t t = slot[ln[a]];
@@ -395,19 +390,19 @@ int oracle_assemble_rows(int64_t n, int64_t E, const double* coord, const int32_
  *   grad_u[m][l] = sum_{i,k} w[i][k] dR[i][k]/du[m][l]
  *   grad_mu      = sum_{i,k} w[i][k] dR[i][k]/dmu
  * Per element, from the Gauss-point form of R_e[a][k] =
- *   sum_g gpvol_g ( rho N_a(g) gpvel_g . grad u^k + mu gpcar_a . grad u^k )
- *   + rho/dt lump_a u[a][k] - b_e[a][k],     grad u^k = sum_c u[c][k] gpcar_c,
+ *   sum_g wq_g ( rho N_a(g) uq_g . grad u^k + mu grad_a . grad u^k )
+ *   + rho/dt lump_a u[a][k] - b_e[a][k],     grad u^k = sum_c u[c][k] grad_c,
  * differentiated term by term:
- *   dR_e[a][k]/du[m][l] = sum_g gpvol_g ( rho N_a(g) N_m(g) (grad u^k)_l
- *                          + delta_kl (rho N_a(g) gpvel_g . gpcar_m + mu gpcar_a . gpcar_m) )
+ *   dR_e[a][k]/du[m][l] = sum_g wq_g ( rho N_a(g) N_m(g) (grad u^k)_l
+ *                          + delta_kl (rho N_a(g) uq_g . grad_m + mu grad_a . grad_m) )
  *                          + delta_kl delta_am rho/dt lump_a
- *   dR_e[a][k]/dmu      = sum_g gpvol_g gpcar_a . grad u^k
+ *   dR_e[a][k]/dmu      = sum_g wq_g grad_a . grad u^k
  * w, u, grad_u are node-major [n][3].  grad_u is overwritten.
  */
 int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
                double rho, double mu, double dt, const double* w, double* grad_u, double* grad_mu) {
-    double shape[PGAUS][PNODE], weight[PGAUS];
-    gauss_rule(shape, weight);
+    double lam[PGAUS][PNODE], wref[PGAUS];
+    quadrature_rule(lam, wref);
     memset(grad_u, 0, sizeof(double) * 3 * n);
     double gmu = 0.0;
     for (int64_t e = 0; e < E; ++e) {
@@ -421,47 +416,47 @@ int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, 
                 U[a][k] = u[3 * (int64_t)ln[a] + k];
                 W[a][k] = w[3 * (int64_t)ln[a] + k];
             }
-        double gpcar[PNODE][NDIME], gpvol[PGAUS];
-        double det = cartesian_derivatives(X, gpcar);
-        for (int g = 0; g < PGAUS; ++g) gpvol[g] = weight[g] * det;
+        double grad[PNODE][NDIME], wq[PGAUS];
+        double det = shape_gradients(X, grad);
+        for (int g = 0; g < PGAUS; ++g) wq[g] = wref[g] * det;
         /* velocity gradient grad u^k (constant on a P1 element) */
         double gradu[NDIME][NDIME]; /* gradu[k][l] = d u^k / d x_l */
         for (int k = 0; k < NDIME; ++k)
             for (int l = 0; l < NDIME; ++l) {
                 gradu[k][l] = 0.0;
-                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * gpcar[c][l];
+                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * grad[c][l];
             }
         for (int g = 0; g < PGAUS; ++g) {
-            double gpvel[NDIME];
+            double uq[NDIME];
             for (int k = 0; k < NDIME; ++k) {
-                gpvel[k] = 0.0;
-                for (int c = 0; c < PNODE; ++c) gpvel[k] += shape[g][c] * U[c][k];
+                uq[k] = 0.0;
+                for (int c = 0; c < PNODE; ++c) uq[k] += lam[g][c] * U[c][k];
             }
             for (int a = 0; a < PNODE; ++a)
                 for (int mm = 0; mm < PNODE; ++mm) {
                     double adv_m = 0.0, visc_am = 0.0;
                     for (int i = 0; i < NDIME; ++i) {
-                        adv_m += gpvel[i] * gpcar[mm][i];
-                        visc_am += gpcar[a][i] * gpcar[mm][i];
+                        adv_m += uq[i] * grad[mm][i];
+                        visc_am += grad[a][i] * grad[mm][i];
                     }
                     for (int k = 0; k < NDIME; ++k)
                         for (int l = 0; l < NDIME; ++l) {
-                            double d = rho * shape[g][a] * shape[g][mm] * gradu[k][l];
-                            if (k == l) d += rho * shape[g][a] * adv_m + mu * visc_am;
-                            grad_u[3 * (int64_t)ln[mm] + l] += W[a][k] * gpvol[g] * d;
+                            double d = rho * lam[g][a] * lam[g][mm] * gradu[k][l];
+                            if (k == l) d += rho * lam[g][a] * adv_m + mu * visc_am;
+                            grad_u[3 * (int64_t)ln[mm] + l] += W[a][k] * wq[g] * d;
                         }
                 }
             for (int a = 0; a < PNODE; ++a)
                 for (int k = 0; k < NDIME; ++k) {
                     double dmu = 0.0;
-                    for (int i = 0; i < NDIME; ++i) dmu += gpcar[a][i] * gradu[k][i];
-                    gmu += W[a][k] * gpvol[g] * dmu;
+                    for (int i = 0; i < NDIME; ++i) dmu += grad[a][i] * gradu[k][i];
+                    gmu += W[a][k] * wq[g] * dmu;
                 }
         }
         /* lumped mass term */
         for (int a = 0; a < PNODE; ++a) {
             double lump = 0.0;
-            for (int g = 0; g < PGAUS; ++g) lump += gpvol[g] * shape[g][a];
+            for (int g = 0; g < PGAUS; ++g) lump += wq[g] * lam[g][a];
             for (int k = 0; k < NDIME; ++k) grad_u[3 * (int64_t)ln[a] + k] += W[a][k] * rho * lump / dt;
         }
     }
@@ -473,7 +468,7 @@ int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, 
  * Condition scale of grad_mu: the sum, over elements e, Gauss points g and
  * node/component pairs (a, k), of the magnitudes of the terms whose sum is
  * grad_mu in oracle_vjp,
- *   sum |w[a][k] gpvol_g (gpcar_a . grad u^k)|.
+ *   sum |w[a][k] wq_g (grad_a . grad u^k)|.
  * A floating-point evaluation of grad_mu in any summation order differs from
  * the exact sum by at most (number of terms) x (rounding unit) x this scale
  * (the standard error bound of a floating-point sum), so comparisons of the
@@ -481,8 +476,8 @@ int oracle_vjp(int64_t n, int64_t E, const double* coord, const int32_t* lnods, 
  */
 int oracle_vjp_mu_abs(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
                       const double* w, double* out) {
-    double shape[PGAUS][PNODE], weight[PGAUS];
-    gauss_rule(shape, weight);
+    double lam[PGAUS][PNODE], wref[PGAUS];
+    quadrature_rule(lam, wref);
     double s = 0.0;
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* ln = lnods + 4 * e;
@@ -495,20 +490,20 @@ int oracle_vjp_mu_abs(int64_t n, int64_t E, const double* coord, const int32_t* 
                 U[a][k] = u[3 * (int64_t)ln[a] + k];
                 W[a][k] = w[3 * (int64_t)ln[a] + k];
             }
-        double gpcar[PNODE][NDIME];
-        const double det = cartesian_derivatives(X, gpcar);
+        double grad[PNODE][NDIME];
+        const double det = shape_gradients(X, grad);
         double gradu[NDIME][NDIME];
         for (int k = 0; k < NDIME; ++k)
             for (int l = 0; l < NDIME; ++l) {
                 gradu[k][l] = 0.0;
-                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * gpcar[c][l];
+                for (int c = 0; c < PNODE; ++c) gradu[k][l] += U[c][k] * grad[c][l];
             }
         for (int g = 0; g < PGAUS; ++g)
             for (int a = 0; a < PNODE; ++a)
                 for (int k = 0; k < NDIME; ++k) {
                     double dmu = 0.0;
-                    for (int i = 0; i < NDIME; ++i) dmu += gpcar[a][i] * gradu[k][i];
-                    s += fabs(W[a][k] * weight[g] * det * dmu);
+                    for (int i = 0; i < NDIME; ++i) dmu += grad[a][i] * gradu[k][i];
+                    s += fabs(W[a][k] * wref[g] * det * dmu);
                 }
     }
     *out = s;
@@ -561,7 +556,7 @@ int oracle_assemble_threads(int64_t n, int64_t E, const double* coord, const int
         for (int64_t e = 0; e < E; ++e) {
             const int32_t* ln = lnods + 4 * e;
             double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME], vol;
-            gather(coord, u, un, ln, X, U, Un);
+            element_nodes(coord, u, un, ln, X, U, Un);
             oracle_element(X, U, Un, rho, mu, dt, (double(*)[PNODE])(Ae + 16 * e),
                            (double(*)[PNODE][NDIME])(Ge + 48 * e), (double(*)[NDIME])(be + 12 * e), &vol);
             for (int a = 0; a < PNODE; ++a)

@@ -284,7 +284,7 @@ def test_rhs_totals():
 
 
 def test_nodal_outputs_closed_forms():
-    """The paper's nodal outputs (rhsid, dt_rho, mass_rho of Listing 2).
+    """The paper's nodal outputs (rhsid, dt_rho, mass_rho of Section II-A).
 
     Unjittered Kuhn cube: every tet has volume h^3/6, so node i receives
     rho h^3/24 per incident tet (counted from the connectivity, no geometry);
