@@ -467,9 +467,10 @@ def fp64_roofline(E, kernel_ms):
 
 def more_workloads(args):
     """Compact records of the largest single-GPU workload (the 200^3 cube in RCM
-    numbering, 48 M tets, mixed32 and mixed64 row gather) and of the batching
-    workload (64 meshes, graph replay): ms per step, elements/s and the HBM
-    roofline fraction of the main kernel."""
+    numbering, 48 M tets, mixed32 and mixed64 row gather), of the batching
+    workload (64 meshes, graph replay) and of the adjoint case (50^3 cube, VJP
+    in FP64 and mixed64): ms per step, elements/s and, for the assembly, the
+    HBM roofline fraction of the main kernel."""
     import torch
 
     import paper_2111_05651_gb300 as nsi
@@ -499,6 +500,8 @@ def more_workloads(args):
     del mesh, u
     torch.cuda.empty_cache()
     out["batch64"] = batch_record(steps=100, warmup=5, precision="mixed64", autotune=True)
+    E, res = adjoint_times(20, 3)
+    out["adjoint50"] = {"workload": WORKLOADS["adjoint50"], "elements": E, "steps": 20, "modes": res}
     out["seconds"] = time.perf_counter() - t_start
     return out
 
@@ -601,13 +604,12 @@ def run_batch(args, world, rank, local):
         }), flush=True)
 
 
-def run_adjoint(args, world, rank, local):
+def adjoint_times(steps, warmup):
+    """The 50^3 adjoint case: ms per VJP call (FP64 and mixed64) and elements/s."""
     import torch
 
     import paper_2111_05651_gb300 as nsi
 
-    torch.cuda.set_device(local)
-    nsi.load_library()
     mesh, u = meshgen.config_mesh("cube50")
     w = meshgen.gaussian_weights(mesh.n_nodes, np.random.default_rng(40))
     res = {}
@@ -616,24 +618,35 @@ def run_adjoint(args, world, rank, local):
         vt = torch.float64 if prec == "fp64" else torch.float32
         ut = torch.as_tensor(u.T.copy()).cuda().to(vt)
         wt = torch.as_tensor(w.T.copy()).cuda().to(vt)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             asm.vjp(ut, wt, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             asm.vjp(ut, wt, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         res[prec] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
         asm.close()
+    return mesh.n_elems, res
+
+
+def run_adjoint(args, world, rank, local):
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    torch.cuda.set_device(local)
+    nsi.load_library()
+    E, res = adjoint_times(args.steps, args.warmup)
     if rank == 0:
         print(json.dumps({"metric": "tet elements differentiated/s (VJP of the assembled residual)",
                           "value": res["mixed64"]["elements_per_s"], "unit": "elements/s", "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["mixed64"]["ms"],
                           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                          "config": {"workload": WORKLOADS["adjoint50"], "elements": mesh.n_elems},
+                          "config": {"workload": WORKLOADS["adjoint50"], "elements": E},
                           "modes": res}), flush=True)
 
 

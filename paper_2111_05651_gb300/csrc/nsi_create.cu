@@ -69,6 +69,8 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->elem_pos);
   cudaFree(h->exact_list);
   cudaFree(h->long_list);
+  cudaFree(h->bad_list);
+  cudaFree(h->bad_mask);
   cudaFree(h->long_ptr);
   cudaFree(h->long_inc);
   cudaFree(h->exact_ptr);
@@ -652,7 +654,7 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
   // nodes) would carry about that ratio times the float rounding of the edge
   // vectors.  The rows of all four nodes of such an element are listed; after
   // the assembly they are recomputed in double (exact_rows_kernel).
-  std::vector<int32_t> exact_list, exact_ptr;
+  std::vector<int32_t> exact_list, exact_ptr, bad_list;
   std::vector<uint32_t> exact_inc;
   if (h->precision != NSI_FP64) {
     std::vector<uint8_t> flag(n, 0);
@@ -668,8 +670,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
         const double had = std::sqrt(dot(d[0], d[0]) * dot(d[1], d[1]) * dot(d[2], d[2]));
         worst = std::max(worst, had / det);
       }
-      if (worst > EXACT_RATIO)
+      if (worst > EXACT_RATIO) {
         for (int a = 0; a < 4; ++a) flag[v[a]] = 1;
+        bad_list.push_back((int32_t)e);
+      }
     }
     for (int64_t i = 0; i < n; ++i)
       if (flag[i] && row_len[i] <= STAR_MAX_ROW) exact_list.push_back((int32_t)i);
@@ -729,6 +733,13 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->long_list, long_list.data(), long_list.size(), s))) return st;
     if ((st = dev_upload(h, &h->long_ptr, long_ptr.data(), long_ptr.size(), s))) return st;
     if ((st = dev_upload(h, &h->long_inc, long_inc.data(), long_inc.size(), s))) return st;
+  }
+  if (!bad_list.empty() && E <= (int64_t)INT32_MAX) {
+    std::vector<uint32_t> mask((size_t)(E + 31) / 32, 0u);
+    for (int32_t e : bad_list) mask[e >> 5] |= 1u << (e & 31);
+    h->n_bad = (int64_t)bad_list.size();
+    if ((st = dev_upload(h, &h->bad_list, bad_list.data(), bad_list.size(), s))) return st;
+    if ((st = dev_upload(h, &h->bad_mask, mask.data(), mask.size(), s))) return st;
   }
   if (h->exact_rows > 0) {
     if ((st = dev_upload(h, &h->exact_list, exact_list.data(), exact_list.size(), s))) return st;

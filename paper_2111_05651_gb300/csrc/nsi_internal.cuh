@@ -184,6 +184,9 @@ struct NsiHandle {
   int32_t* long_list = nullptr;  // [long_rows] their node ids
   int32_t* long_ptr = nullptr;   // [long_rows + 1] into long_inc
   uint32_t* long_inc = nullptr;  // element * 4 + local index of the row's node
+  int64_t n_bad = 0;            // mixed modes: badly shaped elements (the adjoint and residual take them in double)
+  int32_t* bad_list = nullptr;  // [n_bad] their ids
+  uint32_t* bad_mask = nullptr; // [ceil(E / 32)] one bit per element, or null when there are none
   int64_t exact_rows = 0;       // mixed modes: rows recomputed in double (badly shaped elements)
   int32_t* exact_list = nullptr;  // [exact_rows] their node ids
   int32_t* exact_ptr = nullptr;   // [exact_rows + 1] into exact_inc

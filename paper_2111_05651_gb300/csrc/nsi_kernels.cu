@@ -2161,81 +2161,117 @@ __global__ void __launch_bounds__(FAN_BLOCK) batched_fan_kernel(const __grid_con
 }
 
 // ----------------------------------------------------------- VJP kernel ---
-// grad_u[l][v_m] += sum_a w_{a,l} A_e[a][m] + rho/120 sum_k (W_k + w_{m,k}) Gu[k][l]
-// grad_mu       += 1/(6 det) sum_{a,k} w_{a,k} c_a . Gu[k]
+// One element's adjoint terms in arithmetic C (edge vectors d1, d2, d3 from
+// node 0; velocities u and adjoint weights w of the 4 nodes):
+//   g[m] = sum_a w_a A_e[a][m] + rho/120 sum_k (W_k + w_{m,k}) Gu[k]
+//   returned: 1/(6 det) sum_{a,k} w_{a,k} c_a . Gu[k]   (the grad_mu term)
 // with W = sum_a w_a and Gu[k][l] = sum_b u_{b,k} c_b[l] = det du^k/dx_l.
+template <typename C>
+__device__ __forceinline__ C vjp_element(const V3<C>& d1, const V3<C>& d2, const V3<C>& d3, const V3<C> (&u)[4],
+                                         const V3<C> (&w)[4], C kc, C kmu, C kmass, V3<C> (&g)[4]) {
+  V3<C> c[4];
+  c[1] = cross(d2, d3);
+  c[2] = cross(d3, d1);
+  c[3] = cross(d1, d2);
+  const C det = dot(d1, c[1]);
+  c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
+  const V3<C> S = add(add(u[0], u[1]), add(u[2], u[3]));
+  const V3<C> Ws = add(add(w[0], w[1]), add(w[2], w[3]));
+  const C kv = kmu * rcp(det);
+  const C km = det * kmass;
+  V3<C> Gu[3];
+  const C uk[4][3] = {{u[0].x, u[0].y, u[0].z}, {u[1].x, u[1].y, u[1].z}, {u[2].x, u[2].y, u[2].z},
+                      {u[3].x, u[3].y, u[3].z}};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Gu[k] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      Gu[k].x += uk[b][k] * c[b].x;
+      Gu[k].y += uk[b][k] * c[b].y;
+      Gu[k].z += uk[b][k] * c[b].z;
+    }
+  }
+#pragma unroll
+  for (int mm = 0; mm < 4; ++mm) {
+    V3<C> acc = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      C Aam = kc * dot(add(S, u[a]), c[mm]) + kv * dot(c[a], c[mm]);
+      if (a == mm) Aam += km;
+      acc.x += w[a].x * Aam;
+      acc.y += w[a].y * Aam;
+      acc.z += w[a].z * Aam;
+    }
+    const C wk[3] = {Ws.x + w[mm].x, Ws.y + w[mm].y, Ws.z + w[mm].z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc.x += kc * wk[k] * Gu[k].x;
+      acc.y += kc * wk[k] * Gu[k].y;
+      acc.z += kc * wk[k] * Gu[k].z;
+    }
+    g[mm] = acc;
+  }
+  C s = C(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) s += w[a].x * dot(c[a], Gu[0]) + w[a].y * dot(c[a], Gu[1]) + w[a].z * dot(c[a], Gu[2]);
+  return s * (C)(1.0 / 6.0) * rcp(det);
+}
+
+// true if element e is marked in the bit mask of badly shaped elements
+__device__ __forceinline__ bool marked(const uint32_t* __restrict__ mask, int64_t e) {
+  return mask && ((mask[e >> 5] >> (e & 31)) & 1u);
+}
+
+// the element's coordinates, velocities and weights in double (the handle's
+// copy of the coordinates: double, or the float hi + lo pair)
+template <int P>
+__device__ __forceinline__ V3<double> coord64(const MeshView& m, int64_t j) {
+  if constexpr (P == NSI_FP64) {
+    const D4 x = m.xyz64[j];
+    return V3<double>{x.x, x.y, x.z};
+  } else {
+    const float4 h = m.xyz_hi[j], l = m.xyz_lo[j];
+    return V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+  }
+}
+template <typename T>
+__device__ __forceinline__ V3<double> vec64(const void* const* comp, int64_t j) {
+  const V3<T> v = load_vec<T>(comp, j);
+  return V3<double>{(double)v.x, (double)v.y, (double)v.z};
+}
+
+// The adjoint, one element per thread, in the handle's arithmetic; the
+// elements marked in `skip` (badly shaped, mixed modes) are left to
+// vjp_exact_kernel.
 template <int P>
 __global__ void __launch_bounds__(256) vjp_kernel(MeshView m, FieldView f, const void* __restrict__ wv, void* gu,
-                                                  double* gmu) {
+                                                  double* gmu, const uint32_t* __restrict__ skip) {
   using T = typename Prec<P>::T;
   __shared__ T red[32];
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   T my_mu = T(0);
-  if (e < m.E) {
+  if (e < m.E && !marked(skip, e)) {
     const int4 q = m.lnods[e];
     const int v[4] = {q.x, q.y, q.z, q.w};
     const T* W = static_cast<const T*>(wv);
     NodeX<P> X[4];
-    V3<T> u[4], w[4];
+    V3<T> u[4], w[4], g[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       X[a].load(m, v[a]);
       u[a] = load_vec<T>(f.u, v[a]);
       w[a] = {W[v[a]], W[m.n + v[a]], W[2 * m.n + v[a]]};
     }
-    const V3<T> d1 = X[1].minus(X[0]), d2 = X[2].minus(X[0]), d3 = X[3].minus(X[0]);
-    V3<T> c[4];
-    c[1] = cross(d2, d3);
-    c[2] = cross(d3, d1);
-    c[3] = cross(d1, d2);
-    const T det = dot(d1, c[1]);
-    c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
-    const V3<T> S = add(add(u[0], u[1]), add(u[2], u[3]));
-    const V3<T> Ws = add(add(w[0], w[1]), add(w[2], w[3]));
-    const T kc = kc_of<T>(f);
-    const T kv = kmu_of<T>(f) * rcp(det);
-    const T km = det * kmass_of<T>(f);
-    // Gu[k] as vectors over l
-    V3<T> Gu[3];
-    const T uk[4][3] = {{u[0].x, u[0].y, u[0].z}, {u[1].x, u[1].y, u[1].z}, {u[2].x, u[2].y, u[2].z},
-                        {u[3].x, u[3].y, u[3].z}};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      Gu[k] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        Gu[k].x += uk[b][k] * c[b].x;
-        Gu[k].y += uk[b][k] * c[b].y;
-        Gu[k].z += uk[b][k] * c[b].z;
-      }
-    }
-    T* g = static_cast<T*>(gu);
+    my_mu = vjp_element<T>(X[1].minus(X[0]), X[2].minus(X[0]), X[3].minus(X[0]), u, w, kc_of<T>(f), kmu_of<T>(f),
+                           kmass_of<T>(f), g);
+    T* gp = static_cast<T*>(gu);
 #pragma unroll
     for (int mm = 0; mm < 4; ++mm) {
-      V3<T> acc = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        T Aam = kc * dot(add(S, u[a]), c[mm]) + kv * dot(c[a], c[mm]);
-        if (a == mm) Aam += km;
-        acc.x += w[a].x * Aam;
-        acc.y += w[a].y * Aam;
-        acc.z += w[a].z * Aam;
-      }
-      const T wk[3] = {Ws.x + w[mm].x, Ws.y + w[mm].y, Ws.z + w[mm].z};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        acc.x += kc * wk[k] * Gu[k].x;
-        acc.y += kc * wk[k] * Gu[k].y;
-        acc.z += kc * wk[k] * Gu[k].z;
-      }
-      atomicAdd(g + v[mm], acc.x);
-      atomicAdd(g + m.n + v[mm], acc.y);
-      atomicAdd(g + 2 * m.n + v[mm], acc.z);
+      atomicAdd(gp + v[mm], g[mm].x);
+      atomicAdd(gp + m.n + v[mm], g[mm].y);
+      atomicAdd(gp + 2 * m.n + v[mm], g[mm].z);
     }
-    T s = T(0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) s += w[a].x * dot(c[a], Gu[0]) + w[a].y * dot(c[a], Gu[1]) + w[a].z * dot(c[a], Gu[2]);
-    my_mu = s * (T)(1.0 / 6.0) * rcp(det);
   }
   // block reduction of the viscosity sensitivity
   for (int off = 16; off > 0; off >>= 1) my_mu += __shfl_down_sync(0xffffffffu, my_mu, off);
@@ -2251,51 +2287,114 @@ __global__ void __launch_bounds__(256) vjp_kernel(MeshView m, FieldView f, const
   }
 }
 
+// the badly shaped elements of the mixed modes in double (their determinant
+// in float would carry about their shape ratio times the float rounding)
+template <int P>
+__global__ void __launch_bounds__(64) vjp_exact_kernel(MeshView m, FieldView f, const void* __restrict__ wv, void* gu,
+                                                        double* gmu, const int32_t* __restrict__ list, int64_t count) {
+  using T = typename Prec<P>::T;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t e = list[t];
+  const int4 q = m.lnods[e];
+  const int v[4] = {q.x, q.y, q.z, q.w};
+  const void* wc[3] = {static_cast<const T*>(wv), static_cast<const T*>(wv) + m.n, static_cast<const T*>(wv) + 2 * m.n};
+  V3<double> X[4], u[4], w[4], g[4];
+  for (int a = 0; a < 4; ++a) {
+    X[a] = coord64<P>(m, v[a]);
+    u[a] = vec64<T>(f.u, v[a]);
+    w[a] = vec64<T>(wc, v[a]);
+  }
+  const double mu = vjp_element<double>(sub(X[1], X[0]), sub(X[2], X[0]), sub(X[3], X[0]), u, w, f.kc, f.kmu, f.kmass, g);
+  T* gp = static_cast<T*>(gu);
+  for (int mm = 0; mm < 4; ++mm) {
+    atomicAdd(gp + v[mm], (T)g[mm].x);
+    atomicAdd(gp + m.n + v[mm], (T)g[mm].y);
+    atomicAdd(gp + 2 * m.n + v[mm], (T)g[mm].z);
+  }
+  atomicAdd(gmu, mu);
+}
+
 
 // ----------------------------------------------------- residual kernel ---
 // R[k][v_a] += sum_b A_e[a][b] u_b[k] - rho |T_e| / (4 dt) u^n_a[k]: the
 // residual of the assembled system without forming A (element per thread).
+template <typename C>
+__device__ __forceinline__ void residual_element(const V3<C>& d1, const V3<C>& d2, const V3<C>& d3,
+                                                 const V3<C> (&u)[4], const V3<C> (&un)[4], C kc, C kmu, C kmass,
+                                                 V3<C> (&r)[4]) {
+  V3<C> c[4];
+  c[1] = cross(d2, d3);
+  c[2] = cross(d3, d1);
+  c[3] = cross(d1, d2);
+  const C det = dot(d1, c[1]);
+  c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
+  const V3<C> S = add(add(u[0], u[1]), add(u[2], u[3]));
+  const C kv = kmu * rcp(det);
+  const C km = det * kmass;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const V3<C> va = add(S, u[a]);
+    V3<C> ra = {km * (u[a].x - un[a].x), km * (u[a].y - un[a].y), km * (u[a].z - un[a].z)};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const C Aab = kc * dot(va, c[b]) + kv * dot(c[a], c[b]);
+      ra.x += Aab * u[b].x;
+      ra.y += Aab * u[b].y;
+      ra.z += Aab * u[b].z;
+    }
+    r[a] = ra;
+  }
+}
+
 template <int P>
-__global__ void __launch_bounds__(256) residual_kernel(MeshView m, FieldView f, void* rout) {
+__global__ void __launch_bounds__(256) residual_kernel(MeshView m, FieldView f, void* rout,
+                                                       const uint32_t* __restrict__ skip) {
   using T = typename Prec<P>::T;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= m.E) return;
+  if (e >= m.E || marked(skip, e)) return;
   const int4 q = m.lnods[e];
   const int v[4] = {q.x, q.y, q.z, q.w};
   NodeX<P> X[4];
-  V3<T> u[4], un[4];
+  V3<T> u[4], un[4], r[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     X[a].load(m, v[a]);
     u[a] = load_vec<T>(f.u, v[a]);
     un[a] = load_vec<T>(f.un, v[a]);
   }
-  const V3<T> d1 = X[1].minus(X[0]), d2 = X[2].minus(X[0]), d3 = X[3].minus(X[0]);
-  V3<T> c[4];
-  c[1] = cross(d2, d3);
-  c[2] = cross(d3, d1);
-  c[3] = cross(d1, d2);
-  const T det = dot(d1, c[1]);
-  c[0] = {-(c[1].x + c[2].x + c[3].x), -(c[1].y + c[2].y + c[3].y), -(c[1].z + c[2].z + c[3].z)};
-  const V3<T> S = add(add(u[0], u[1]), add(u[2], u[3]));
-  const T kc = kc_of<T>(f);
-  const T kv = kmu_of<T>(f) * rcp(det);
-  const T km = det * kmass_of<T>(f);
+  residual_element<T>(X[1].minus(X[0]), X[2].minus(X[0]), X[3].minus(X[0]), u, un, kc_of<T>(f), kmu_of<T>(f),
+                      kmass_of<T>(f), r);
   T* R = static_cast<T*>(rout);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const V3<T> va = add(S, u[a]);
-    V3<T> r = {km * (u[a].x - un[a].x), km * (u[a].y - un[a].y), km * (u[a].z - un[a].z)};
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const T Aab = kc * dot(va, c[b]) + kv * dot(c[a], c[b]);
-      r.x += Aab * u[b].x;
-      r.y += Aab * u[b].y;
-      r.z += Aab * u[b].z;
-    }
-    atomicAdd(R + v[a], r.x);
-    atomicAdd(R + m.n + v[a], r.y);
-    atomicAdd(R + 2 * m.n + v[a], r.z);
+    atomicAdd(R + v[a], r[a].x);
+    atomicAdd(R + m.n + v[a], r[a].y);
+    atomicAdd(R + 2 * m.n + v[a], r[a].z);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(64) residual_exact_kernel(MeshView m, FieldView f, void* rout,
+                                                             const int32_t* __restrict__ list, int64_t count) {
+  using T = typename Prec<P>::T;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t e = list[t];
+  const int4 q = m.lnods[e];
+  const int v[4] = {q.x, q.y, q.z, q.w};
+  V3<double> X[4], u[4], un[4], r[4];
+  for (int a = 0; a < 4; ++a) {
+    X[a] = coord64<P>(m, v[a]);
+    u[a] = vec64<T>(f.u, v[a]);
+    un[a] = vec64<T>(f.un, v[a]);
+  }
+  residual_element<double>(sub(X[1], X[0]), sub(X[2], X[0]), sub(X[3], X[0]), u, un, f.kc, f.kmu, f.kmass, r);
+  T* R = static_cast<T*>(rout);
+  for (int a = 0; a < 4; ++a) {
+    atomicAdd(R + v[a], (T)r[a].x);
+    atomicAdd(R + m.n + v[a], (T)r[a].y);
+    atomicAdd(R + 2 * m.n + v[a], (T)r[a].z);
   }
 }
 
@@ -2712,8 +2811,11 @@ static nsi_status vjp_p(NsiHandle* h, const FieldView& f, const void* w, void* g
   NSI_CUDA(cudaMemsetAsync(gmu, 0, sizeof(double), s));
   if (h->E == 0) return NSI_OK;
   const int blk = 256;
-  vjp_kernel<P><<<(h->E + blk - 1) / blk, blk, 0, s>>>(view_of(h), f, w, gu, gmu);
-  return check_launch("vjp_kernel");
+  vjp_kernel<P><<<(h->E + blk - 1) / blk, blk, 0, s>>>(view_of(h), f, w, gu, gmu, h->bad_mask);
+  nsi_status st = check_launch("vjp_kernel");
+  if (st || h->n_bad == 0) return st;
+  vjp_exact_kernel<P><<<(h->n_bad + 63) / 64, 64, 0, s>>>(view_of(h), f, w, gu, gmu, h->bad_list, h->n_bad);
+  return check_launch("vjp_exact_kernel");
 }
 
 
@@ -2723,8 +2825,11 @@ static nsi_status residual_p(NsiHandle* h, const FieldView& f, void* r, cudaStre
   NSI_CUDA(cudaMemsetAsync(r, 0, sizeof(T) * 3 * h->n, s));
   if (h->E == 0) return NSI_OK;
   const int blk = 256;
-  residual_kernel<P><<<(h->E + blk - 1) / blk, blk, 0, s>>>(view_of(h), f, r);
-  return check_launch("residual_kernel");
+  residual_kernel<P><<<(h->E + blk - 1) / blk, blk, 0, s>>>(view_of(h), f, r, h->bad_mask);
+  nsi_status st = check_launch("residual_kernel");
+  if (st || h->n_bad == 0) return st;
+  residual_exact_kernel<P><<<(h->n_bad + 63) / 64, 64, 0, s>>>(view_of(h), f, r, h->bad_list, h->n_bad);
+  return check_launch("residual_exact_kernel");
 }
 
 int gather_kernel_regs(int precision) {

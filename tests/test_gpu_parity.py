@@ -455,6 +455,32 @@ def _sliver_mesh():
 
 
 @pytest.mark.parametrize("precision", ["mixed64", "mixed32"])
+def test_badly_shaped_elements_in_the_adjoint_and_residual(precision):
+    """The sliver mesh through nsi_assemble_vjp and nsi_residual in a mixed
+    precision: the badly shaped elements are taken in double (a float
+    determinant would carry ~1e3 float roundings), so both match the oracle
+    on the float velocities at the mixed bar (grad_mu relative to the sum of
+    its terms' magnitudes)."""
+    mesh, u = _sliver_mesh()
+    w = np.random.default_rng(97).standard_normal(u.shape)
+    un = np.random.default_rng(98).standard_normal(u.shape)
+    asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    assert asm.info().exact_rows > 0
+    gu, gmu = asm.vjp(torch.as_tensor(u.T.copy()), torch.as_tensor(w.T.copy()))
+    R = asm.residual(torch.as_tensor(u.T.copy()), u_n=torch.as_tensor(un.T.copy())).double().cpu().numpy()
+    asm.close()
+    uo, wo, uno = (x.astype(np.float32).astype(np.float64) for x in (u, w, un))
+    ogu, ogmu = oracle.vjp(mesh.coord, mesh.lnods, uo, wo, RHO, MU, DT)
+    gu = gu.double().cpu().numpy().T
+    assert np.abs(gu - ogu).max() <= 1e-5 * np.abs(ogu).max()
+    gabs = oracle.vjp_mu_abs(mesh.coord, mesh.lnods, uo, wo, RHO, MU, DT)
+    assert abs(float(gmu.item()) - ogmu) <= 1e-5 * gabs
+    rp, ci, oA, oG, orhs = oracle.assemble(mesh.coord, mesh.lnods, uo, uno)
+    Ro = oracle.residual((rp, ci, oA), orhs, uo)
+    assert np.abs(R.T - Ro).max() <= 1e-5 * np.abs(Ro).max()
+
+
+@pytest.mark.parametrize("precision", ["mixed64", "mixed32"])
 def test_badly_shaped_elements_use_double_determinants(precision):
     mesh, u = _sliver_mesh()
     asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision, scatter="gather")
