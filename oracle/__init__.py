@@ -70,6 +70,17 @@ def _load():
                                        ctypes.c_double, ctypes.c_double, _d, _d, _d]
             lib.oracle_assemble_threads.restype = ctypes.c_int
             lib.oracle_assemble_threads.argtypes = lib.oracle_assemble.argtypes + [ctypes.c_int]
+            lib.oracle_assemble_stabilized.restype = ctypes.c_int
+            lib.oracle_assemble_stabilized.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, _d,
+                                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, _i32, _i32,
+                                                       _d, _d, _d]
+            lib.oracle_stab_rows.restype = ctypes.c_int
+            lib.oracle_stab_rows.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, ctypes.c_double,
+                                             ctypes.c_double, _i64, ctypes.c_int64, ctypes.c_int64, _i32, _i32, _d]
+            lib.oracle_stab_element.restype = None
+            lib.oracle_stab_element.argtypes = [_d, _d, ctypes.c_double, ctypes.c_double, _d, _d]
+            lib.oracle_tau.restype = ctypes.c_double
+            lib.oracle_tau.argtypes = [_d, _d, ctypes.c_double, ctypes.c_double, _d]
             lib.oracle_vjp_mu_abs.restype = ctypes.c_int
             lib.oracle_vjp_mu_abs.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, _d, _d]
             _lib = lib
@@ -137,6 +148,68 @@ def assemble(coord, lnods, u, un=None, rho=1.0, mu=1e-3, dt=1e-2, csr=None):
     if rc != 0:
         raise ValueError(f"oracle_assemble failed ({rc})")
     return row_ptr, col_idx, A, G, rhs
+
+
+def tau(X, U, rho=1.0, mu=1e-3):
+    """(tau1, tau2) of one element (X, U: [4, 3]); see ``oracle_tau``."""
+    lib = _load()
+    t2 = np.zeros(1)
+    t1 = lib.oracle_tau(_p(_f64(X), _d), _p(_f64(U), _d), rho, mu, _p(t2, _d))
+    return float(t1), float(t2[0])
+
+
+def stab_element(X, U, rho=1.0, mu=1e-3):
+    """(S [4, 4], K [4, 4, 3, 3]) of one element; see ``oracle_stab_element``."""
+    lib = _load()
+    S = np.empty((4, 4)); K = np.empty((4, 4, 3, 3))
+    lib.oracle_stab_element(_p(_f64(X), _d), _p(_f64(U), _d), rho, mu, _p(S, _d), _p(K, _d))
+    return S, K
+
+
+def assemble_stabilized(coord, lnods, u, un=None, rho=1.0, mu=1e-3, dt=1e-2, csr=None):
+    """Stabilised assembly -> (row_ptr, col_idx, Auu [9, nnz], G [3, nnz],
+    rhs [3, n]); Auu[3 i + j] is the (i, j) entry of every 3x3 block (see
+    ``oracle_assemble_stabilized``)."""
+    lib = _load()
+    coord, lnods, u = _f64(coord), _ln(lnods), _f64(u)
+    un = u if un is None else _f64(un)
+    n = coord.shape[0]
+    row_ptr, col_idx = pattern(n, lnods) if csr is None else csr
+    nnz = int(row_ptr[-1])
+    Auu = np.empty((9, nnz)); G = np.empty((3, nnz)); rhs = np.empty((3, n))
+    rc = lib.oracle_assemble_stabilized(n, lnods.shape[0], _p(coord, _d), _p(lnods, _i32), _p(u, _d), _p(un, _d),
+                                        rho, mu, dt, _p(_ln(row_ptr), _i32), _p(_ln(col_idx), _i32),
+                                        _p(Auu, _d), _p(G, _d), _p(rhs, _d))
+    if rc != 0:
+        raise ValueError(f"oracle_assemble_stabilized failed ({rc})")
+    return row_ptr, col_idx, Auu, G, rhs
+
+
+def assemble_stabilized_rows(coord, lnods, u, rows, un=None, rho=1.0, mu=1e-3, dt=1e-2, maxc=64):
+    """Stabilised rows for a list of row ids -> list of (cols, Auu [9, c],
+    G [3, c], rhs [3]): the Galerkin rows of ``assemble_rows`` on the diagonal
+    components plus the stabilisation of ``oracle_stab_rows``."""
+    lib = _load()
+    gal = assemble_rows(coord, lnods, u, rows, un=un, rho=rho, mu=mu, dt=dt, maxc=maxc)
+    coord, lnods, u = _f64(coord), _ln(lnods), _f64(u)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    m = rows.size
+    cols = np.zeros((m, maxc), dtype=np.int32); count = np.zeros(m, dtype=np.int32)
+    Auu = np.zeros((m, 9, maxc))
+    rc = lib.oracle_stab_rows(coord.shape[0], lnods.shape[0], _p(coord, _d), _p(lnods, _i32), _p(u, _d), rho, mu,
+                              _p(rows, _i64), m, maxc, _p(cols, _i32), _p(count, _i32), _p(Auu, _d))
+    if rc != 0:
+        raise ValueError(f"oracle_stab_rows failed ({rc})")
+    out = []
+    for t in range(m):
+        c, A, G, rhs = gal[t]
+        if not np.array_equal(c, cols[t, :count[t]]):
+            raise ValueError("oracle_stab_rows: columns differ from the Galerkin row")
+        blk = Auu[t, :, :count[t]].copy()
+        for i in range(3):
+            blk[4 * i] += A
+        out.append((c, blk, G, rhs))
+    return out
 
 
 def assemble_threads(coord, lnods, u, un=None, rho=1.0, mu=1e-3, dt=1e-2, csr=None, threads=0):

@@ -591,3 +591,172 @@ int oracle_assemble_threads(int64_t n, int64_t E, const double* coord, const int
     free(first); free(inc); free(Ae); free(Ge); free(be); free(pos);
     return rc;
 }
+
+/*
+ * The stabilised momentum operator: the block of the velocity unknowns,
+ * (PNODE x NDIME)^2 per element, as the paper's 12x12 element matrix (Section
+ * II-A, Listing 4: every pair of dimensions coupled, equal dimensions receiving
+ * the scalar part).  For element e, nodes a, b and dimensions i, j
+ *
+ *   Auu[(a,i),(b,j)] = delta_ij ( A_e[a][b] + S_e[a][b] ) + K_e[a][b][i][j]
+ *
+ * with A_e the Galerkin element matrix (convection, viscosity, lumped mass)
+ * and the terms of the algebraic subgrid-scale stabilisation of R. Codina,
+ * Comput. Methods Appl. Mech. Engrg. 191 (2002) 4295-4321 (linear elements,
+ * c1 = 4, c2 = 2), taken implicitly (the projection of that method's
+ * orthogonal subscales belongs to the right-hand side and is not built here):
+ *   tau1_e = ( c1 mu / h_e^2 + c2 rho |ubar_e| / h_e )^{-1}
+ *   tau2_e = h_e^2 / (c1 tau1_e)
+ *   S_e[a][b]        = tau1_e rho^2 int (u_h . grad N_a)(u_h . grad N_b)
+ *   K_e[a][b][i][j]  = mu int d_j N_a d_i N_b      (the transposed-gradient
+ *                      half of the viscous stress mu (grad u + grad u^T))
+ *                    + tau2_e int d_i N_a d_j N_b  (the grad-div term of the
+ *                      pressure subscale)
+ * with h_e = (6 |T_e|)^{1/3} and ubar_e the mean of the element's node
+ * velocities u.  S is integrated with the 4-point rule (its integrand has
+ * degree 2); the integrands of K are constant.
+ */
+double oracle_tau(const double X[PNODE][NDIME], const double U[PNODE][NDIME], double rho, double mu, double* tau2) {
+    double grad[PNODE][NDIME];
+    const double det = shape_gradients(X, grad);
+    const double h = cbrt(det); /* det = 6 |T| */
+    double ub[NDIME] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < PNODE; ++c)
+        for (int k = 0; k < NDIME; ++k) ub[k] += U[c][k] / PNODE;
+    const double speed = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    const double c1 = 4.0, c2 = 2.0;
+    const double tau1 = 1.0 / (c1 * mu / (h * h) + c2 * rho * speed / h);
+    if (tau2) *tau2 = h * h / (c1 * tau1);
+    return tau1;
+}
+
+void oracle_stab_element(const double X[PNODE][NDIME], const double U[PNODE][NDIME], double rho, double mu,
+                         double S[PNODE][PNODE], double K[PNODE][PNODE][NDIME][NDIME]) {
+    double lam[PGAUS][PNODE], wref[PGAUS];
+    quadrature_rule(lam, wref);
+    double grad[PNODE][NDIME];
+    const double det = shape_gradients(X, grad);
+    double tau2;
+    const double tau1 = oracle_tau(X, U, rho, mu, &tau2);
+    memset(S, 0, sizeof(double) * PNODE * PNODE);
+    for (int q = 0; q < PGAUS; ++q) {
+        double uq[NDIME] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < NDIME; ++k)
+            for (int c = 0; c < PNODE; ++c) uq[k] += lam[q][c] * U[c][k];
+        double adv[PNODE];
+        for (int a = 0; a < PNODE; ++a) {
+            adv[a] = 0.0;
+            for (int k = 0; k < NDIME; ++k) adv[a] += uq[k] * grad[a][k];
+        }
+        for (int a = 0; a < PNODE; ++a)
+            for (int b = 0; b < PNODE; ++b) S[a][b] += wref[q] * det * tau1 * rho * rho * adv[a] * adv[b];
+    }
+    const double vol = det / 6.0;
+    for (int a = 0; a < PNODE; ++a)
+        for (int b = 0; b < PNODE; ++b)
+            for (int i = 0; i < NDIME; ++i)
+                for (int j = 0; j < NDIME; ++j)
+                    K[a][b][i][j] = mu * vol * grad[a][j] * grad[b][i] + tau2 * vol * grad[a][i] * grad[b][j];
+}
+
+/*
+ * Stabilised assembly on the CSR pattern: Auu [9][nnz] with component 3 i + j
+ * the (i, j) entry of the 3x3 block of (row node, column node), G [3][nnz] and
+ * rhs [3][n] as oracle_assemble.  Elements in increasing order.
+ */
+int oracle_assemble_stabilized(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u,
+                               const double* un, double rho, double mu, double dt, const int32_t* row_ptr,
+                               const int32_t* col_idx, double* Auu, double* G, double* rhs) {
+    const int64_t nnz = row_ptr[n];
+    double* A = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!A) return -4;
+    int rc = oracle_assemble(n, E, coord, lnods, u, un, rho, mu, dt, row_ptr, col_idx, A, G, rhs);
+    if (rc != 0) {
+        free(A);
+        return rc;
+    }
+    memset(Auu, 0, sizeof(double) * 9 * (size_t)nnz);
+    for (int64_t p = 0; p < nnz; ++p)
+        for (int i = 0; i < NDIME; ++i) Auu[(4 * i) * nnz + p] = A[p];
+    free(A);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
+        double Se[PNODE][PNODE], Ke[PNODE][PNODE][NDIME][NDIME];
+        element_nodes(coord, u, un, ln, X, U, Un);
+        oracle_stab_element(X, U, rho, mu, Se, Ke);
+        for (int a = 0; a < PNODE; ++a)
+            for (int c = 0; c < PNODE; ++c) {
+                const int64_t pos = find_pos(row_ptr, col_idx, ln[a], ln[c]);
+                if (pos < 0) return -3;
+                for (int i = 0; i < NDIME; ++i)
+                    for (int j = 0; j < NDIME; ++j)
+                        Auu[(3 * i + j) * nnz + pos] += (i == j ? Se[a][c] : 0.0) + Ke[a][c][i][j];
+            }
+    }
+    return 0;
+}
+
+/*
+ * The stabilisation part alone (S on the diagonal components, K on all nine)
+ * restricted to a list of rows, for spot checks on meshes too large for the
+ * full oracle: for sampled row t, cols[t*maxc ...] its columns (ascending),
+ * count[t] their number, Auu[(t*9 + 3 i + j)*maxc + q] the values.
+ * Contributions are added in increasing element order.
+ */
+int oracle_stab_rows(int64_t n, int64_t E, const double* coord, const int32_t* lnods, const double* u, double rho,
+                     double mu, const int64_t* rows, int64_t m, int64_t maxc, int32_t* cols, int32_t* count,
+                     double* Auu) {
+    int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    if (!slot) return -2;
+    for (int64_t i = 0; i < n; ++i) slot[i] = -1;
+    for (int64_t t = 0; t < m; ++t) {
+        if (rows[t] < 0 || rows[t] >= n || slot[rows[t]] >= 0) { free(slot); return -1; }
+        slot[rows[t]] = t;
+        count[t] = 0;
+    }
+    memset(Auu, 0, sizeof(double) * m * 9 * maxc);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ln = lnods + 4 * e;
+        int hit = 0;
+        for (int a = 0; a < PNODE; ++a) {
+            if (ln[a] < 0 || ln[a] >= n) { free(slot); return -1; }
+            hit |= slot[ln[a]] >= 0;
+        }
+        if (!hit) continue;
+        double X[PNODE][NDIME], U[PNODE][NDIME], Un[PNODE][NDIME];
+        double Se[PNODE][PNODE], Ke[PNODE][PNODE][NDIME][NDIME];
+        element_nodes(coord, u, u, ln, X, U, Un);
+        oracle_stab_element(X, U, rho, mu, Se, Ke);
+        for (int a = 0; a < PNODE; ++a) {
+            const int64_t t = slot[ln[a]];
+            if (t < 0) continue;
+            for (int c = 0; c < PNODE; ++c) {
+                int64_t q = 0;
+                while (q < count[t] && cols[t * maxc + q] != ln[c]) ++q;
+                if (q == count[t]) {
+                    if (q >= maxc) { free(slot); return -4; }
+                    cols[t * maxc + q] = ln[c];
+                    count[t] += 1;
+                }
+                for (int i = 0; i < NDIME; ++i)
+                    for (int j = 0; j < NDIME; ++j)
+                        Auu[(t * 9 + 3 * i + j) * maxc + q] += (i == j ? Se[a][c] : 0.0) + Ke[a][c][i][j];
+            }
+        }
+    }
+    for (int64_t t = 0; t < m; ++t) {
+        for (int32_t q = 1; q < count[t]; ++q) {
+            for (int32_t r = q; r > 0 && cols[t * maxc + r - 1] > cols[t * maxc + r]; --r) {
+                const int64_t i0 = t * maxc + r - 1, i1 = t * maxc + r;
+                const int32_t tc = cols[i0]; cols[i0] = cols[i1]; cols[i1] = tc;
+                for (int k = 0; k < 9; ++k) {
+                    const int64_t j0 = (t * 9 + k) * maxc + r - 1, j1 = j0 + 1;
+                    const double tv = Auu[j0]; Auu[j0] = Auu[j1]; Auu[j1] = tv;
+                }
+            }
+        }
+    }
+    free(slot);
+    return 0;
+}
