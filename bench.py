@@ -39,6 +39,9 @@ WORKLOADS = {
     "step100": "Kuhn cube 100^3 hexes, 6,000,000 tets, jitter 15% h, random numbering, seed 1: one time step with "
                "cached geometry, A = A_static + C(u) and rhs (A_static and G assembled once, outside the timing)",
     "cube100": "Kuhn cube 100^3 hexes, 6,000,000 tets, 1,030,301 nodes, jitter 15% h, random numbering, seed 1",
+    "stab100": "stabilised velocity block (3x3 block per CSR entry: Galerkin part, SUPG product, transposed-"
+               "gradient viscous coupling, grad-div term; Codina's tau1, tau2) of the 100^3 cube: 6,000,000 tets, "
+               "jitter 15% h, random numbering, seed 1",
     "cube8": "Kuhn cube 8^3 hexes, 3,072 tets, 729 nodes, natural numbering, seed 0",
     "cube70": "Kuhn cube 70^3 hexes, 2,058,000 tets, 357,911 nodes, jitter 15% h, random numbering, seed 1 "
               "(profiling case: the 100^3 recipe with outputs still above L2)",
@@ -53,6 +56,104 @@ def algorithmic_bytes(E, n, nnz, precision):
     velocities, CSR pattern (row_ptr + col_idx), A + 3 G value arrays, 3 rhs."""
     sx, su, so = PREC_BYTES[precision]
     return 16 * E + n * (3 * sx + 3 * su) + 4 * (n + 1) + 4 * nnz + so * 4 * nnz + so * 3 * n
+
+
+def stab_bytes(E, n, nnz, precision):
+    """Compulsory HBM bytes of one stabilised-block assembly: connectivity 16 B/tet,
+    coordinates, velocities, CSR pattern, Auu (9 values per entry) + 3 G value
+    arrays, 3 rhs."""
+    sx, su, so = PREC_BYTES[precision]
+    return 16 * E + n * (3 * sx + 3 * su) + 4 * (n + 1) + 4 * nnz + so * 12 * nnz + so * 3 * n
+
+
+def stab_times(mesh, u, precs, steps, warmup, flush, stream, rows=None):
+    """Per precision: ms per nsi_assemble_stabilized call and of its main kernel
+    (L2 flushed before every step), elements/s, the HBM roofline of the kernel
+    and the largest row-scaled error of sampled rows against the oracle."""
+    import torch
+
+    import oracle
+    import paper_2111_05651_gb300 as nsi
+
+    E, n = mesh.n_elems, mesh.n_nodes
+    peak, _ = hbm_peak()
+    res = {}
+    for prec in precs:
+        asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=prec)
+        vt = torch.float64 if prec == "fp64" else torch.float32
+        ut = torch.as_tensor(u.T.copy()).to("cuda", vt).contiguous()
+        out = (torch.empty(9, asm.nnz, dtype=asm.out_dtype, device="cuda"),
+               torch.empty(3, asm.nnz, dtype=asm.out_dtype, device="cuda"),
+               torch.empty(3, n, dtype=asm.out_dtype, device="cuda"))
+        fn = lambda: asm.assemble_stabilized(ut, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, out=out)  # noqa
+        ms, kms = time_steps(asm, fn, steps if prec != "fp64" else max(3, min(steps, 5)), warmup, flush, stream)
+        km = statistics.mean(kms)
+        nb = stab_bytes(E, n, asm.nnz, prec)
+        rec = {"ms": statistics.mean(ms), "kernel_ms": km, "elements_per_s": E / (statistics.mean(ms) * 1e-3),
+               "algorithmic_bytes": nb, "achieved_gbs": nb / (km * 1e-3) / 1e9,
+               "roofline_frac": nb / (km * 1e-3) / 1e9 / peak, "fan_kernel": bool(asm.info().fan_ok),
+               "launches_per_step": 2 if asm.info().fan_ok else 1}
+        if rows is not None:
+            uo = u if prec == "fp64" else u.astype(np.float32).astype(np.float64)
+            ref = oracle.assemble_stabilized_rows(mesh.coord, mesh.lnods, uo, rows, None, meshgen.RHO, meshgen.MU,
+                                                  meshgen.DT)
+            rp = asm.pattern()[0].cpu().numpy()
+            Auu, G, rh = (t.double().cpu().numpy() for t in out)
+            err = 0.0
+            for r, (cols, blk, g, orh) in zip(rows, ref):
+                s_, e_ = rp[r], rp[r + 1]
+                for c in range(9):
+                    err = max(err, np.abs(Auu[c, s_:e_] - blk[c]).max() / np.abs(blk[c]).max())
+                for d in range(3):
+                    err = max(err, np.abs(G[d, s_:e_] - g[d]).max() / np.abs(g[d]).max())
+                err = max(err, np.abs(rh[:, r] - orh).max() / np.abs(rh).max())
+            rec["max_rel_err"] = float(err)
+        res[prec] = rec
+        asm.close()
+        del out
+    return res
+
+
+def run_stab(args, world, rank, local):
+    import torch
+
+    import paper_2111_05651_gb300 as nsi
+
+    torch.cuda.set_device(local)
+    nsi.load_library()
+    mesh, u = meshgen.config_mesh("cube100")
+    E, n = mesh.n_elems, mesh.n_nodes
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(9).integers(0, n, 24)]))
+    precs = [args.precision] + ([p for p in ("mixed32", "mixed64", "fp64") if p != args.precision]
+                                if not args.quick else [])
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    res = stab_times(mesh, u, precs, args.steps, args.warmup, lambda: flush_buf.fill_(1),
+                     torch.cuda.current_stream(), rows)
+    barrier(world)
+    clocks = sampler.stop()
+    m = res[args.precision]
+    ms = allreduce_max(m["ms"], world)
+    if rank == 0:
+        peak, src = hbm_peak()
+        print(json.dumps({"metric": "tet elements assembled/s (stabilised velocity block)",
+                          "value": world * E / (ms * 1e-3), "unit": "elements/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None,
+                          "dtype": {"fp64": "f64", "mixed64": "f32", "mixed32": "f32"}[args.precision],
+                          "data": "synthetic",
+                          "config": {"workload": WORKLOADS["stab100"], "precision": args.precision,
+                                     "elements": E, "nodes": n,
+                                     "l2": "flushed (256 MiB write) before every timed step"},
+                          "roofline": {"bound": "hbm", "achieved": m["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                                       "frac": m["achieved_gbs"] / peak,
+                                       "traffic": read_traffic("stab_fan_kernel", "cube100", args.precision),
+                                       "kernel": "stab_fan_kernel", "algorithmic_bytes": m["algorithmic_bytes"],
+                                       "kernel_ms": m["kernel_ms"], "peak_source": src},
+                          "clocks": clocks, "gpu_launches": args.steps * m["launches_per_step"],
+                          "max_rel_err": m.get("max_rel_err"), "modes": res}), flush=True)
 
 
 def csrc_hash():
@@ -420,7 +521,7 @@ def run_gpu(args, world, rank, local):
         line["cpu_baseline_1core"] = {"value": rate1, "unit": "elements/s", "cores": 1, "kind": "oracle",
                                       "sample": f"the same sample, serial oracle, median of 3 runs of {med1:.2f} s"}
     if world == 1 and not args.no_extras and args.workload == "cube100":
-        line["more_workloads"] = more_workloads(args)
+        line["more_workloads"] = more_workloads(args, (mesh, u))
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -465,12 +566,13 @@ def fp64_roofline(E, kernel_ms):
             "flops_per_tet": FP64_FLOPS_PER_TET, "kernel_ms": kernel_ms, "peak_source": src}
 
 
-def more_workloads(args):
+def more_workloads(args, mesh100=None):
     """Compact records of the largest single-GPU workload (the 200^3 cube in RCM
-    numbering, 48 M tets, mixed32 and mixed64 row gather), of the batching
-    workload (64 meshes, graph replay) and of the adjoint case (50^3 cube, VJP
-    in FP64 and mixed64): ms per step, elements/s and, for the assembly, the
-    HBM roofline fraction of the main kernel."""
+    numbering, 48 M tets, mixed32 and mixed64 row gather), of the stabilised
+    velocity block on the 100^3 cube (mixed64), of the batching workload (64
+    meshes, graph replay) and of the adjoint case (50^3 cube, VJP in FP64 and
+    mixed64): ms per step, elements/s and, for the assemblies, the HBM
+    roofline fraction of the main kernel."""
     import torch
 
     import paper_2111_05651_gb300 as nsi
@@ -499,6 +601,10 @@ def more_workloads(args):
     out["cube200_rcm"] = rec
     del mesh, u
     torch.cuda.empty_cache()
+    if mesh100 is not None:
+        res = stab_times(mesh100[0], mesh100[1], ("mixed64",), 20, 3, lambda: flush_buf.fill_(1), stream)
+        out["stab100"] = {"workload": WORKLOADS["stab100"], "elements": mesh100[0].n_elems, "steps": 20,
+                          "modes": res}
     out["batch64"] = batch_record(steps=100, warmup=5, precision="mixed64", autotune=True)
     E, res = adjoint_times(20, 3)
     out["adjoint50"] = {"workload": WORKLOADS["adjoint50"], "elements": E, "steps": 20, "modes": res}
@@ -789,6 +895,8 @@ def main():
             run_adjoint(args, world, rank, local)
         elif args.workload == "step100":
             run_step(args, world, rank, local)
+        elif args.workload == "stab100":
+            run_stab(args, world, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:

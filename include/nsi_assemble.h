@@ -53,7 +53,7 @@
  *  - Outputs are OVERWRITTEN by every assemble call (the call defines every
  *    entry; no prior zeroing is needed).
  *  - The device entry points (nsi_assemble, _mode, _batched, _convective,
- *    _nodal, _vjp, nsi_residual) never allocate device memory, never
+ *    _nodal, _stabilized, _vjp, nsi_residual) never allocate device memory, never
  *    synchronise the stream, and only enqueue work on the given stream; they
  *    may be captured into a CUDA graph.  nsi_assemble_host, for host buffers,
  *    is the exception (see its comment).  Errors detected on the device (only when the handle
@@ -190,6 +190,10 @@ typedef struct {
                                encoder could not cover -- computed after every row-gather
                                assembly or time step by one thread per row, in double; the rest
                                of the mesh stays on the row gather */
+    int32_t fan_ok;         /* 1: the mesh has an edge-fan map (rows of at most 16 entries, the
+                               ring of elements around every edge at most 7 nodes, no long
+                               rows): the edge-fan kernel and the stabilised block's fan kernel
+                               are available */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 
@@ -250,6 +254,39 @@ nsi_status nsi_assemble_convective(NsiHandle* h, const NsiFields* f, const void*
  */
 nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void* dt_rho, void* mass_rho,
                               void* stream);
+
+/*
+ * The stabilised velocity block.  Paper Section II-A, Listing 4: the 12x12
+ * element matrix of the velocity unknowns couples every pair of dimensions of
+ * two nodes, equal dimensions receiving the scalar part; Table I's
+ * calculate_tau_and_tim computes the stabilisation parameters, whose formulas
+ * the paper does not print.  This library's reading: the Galerkin operator
+ * above plus the implicit terms of Codina's algebraic subgrid scales
+ * (Comput. Methods Appl. Mech. Engrg. 191 (2002) 4295-4321; linear elements,
+ * c1 = 4, c2 = 2), per element
+ *   tau1 = (4 mu / h^2 + 2 rho |ubar| / h)^-1,  tau2 = h^2 / (4 tau1),
+ *   h = (6 |T_e|)^(1/3),  ubar = the mean of the element's four node velocities,
+ *   Auu_e(a,i; b,j) = delta_ij ( A_e[a][b] + tau1 rho^2 int (u.grad N_a)(u.grad N_b) )
+ *                   + mu int d_j N_a d_i N_b + tau2 int d_i N_a d_j N_b
+ * (the SUPG convection product, the transposed-gradient half of the viscous
+ * stress, the grad-div term of the pressure subscale).
+ * Outputs (device, overwritten; double for NSI_FP64 and NSI_MIXED_F32_ACC64,
+ * float for NSI_MIXED_F32_ACC32):
+ *   Auu   [9][nnz]: component 3 i + j is the (i, j) entry of the 3x3 block
+ *                   of every CSR entry (row node's dimension i, column
+ *                   node's dimension j);
+ *   G_val [3][nnz] and rhs [3][n_nodes]: as nsi_assemble.
+ * Meshes with an edge-fan map (NsiInfo.fan_ok) run one thread per CSR entry;
+ * the mixed modes then recompute the rows touching badly shaped elements in
+ * double.  Other meshes run one double-precision thread per row.  Precision
+ * as nsi_assemble; in NSI_MIXED_F32_ACC64 the diagonal components are
+ * compensated float pairs, the six others and G float sums.  The handle's
+ * scatter mode does not apply.  Requires mu > 0 (tau1 of an element at rest
+ * is h^2 / (4 mu)), rho >= 0, dt > 0 (NSI_ERR_INVALID_ARG otherwise).
+ * Never allocates or synchronises.
+ */
+nsi_status nsi_assemble_stabilized(NsiHandle* h, const NsiFields* f, void* Auu, void* G_val, void* rhs,
+                                   void* stream);
 
 /*
  * Vector-Jacobian product of the assembled residual R(u, mu) = A(u) u - b

@@ -28,7 +28,7 @@ __all__ = [
     "load_library", "library_path", "exported_symbols",
     "nsi_assemble_create", "nsi_assemble_destroy", "nsi_csr_pattern", "nsi_csr_pattern_copy", "nsi_info",
     "nsi_assemble", "nsi_assemble_mode", "nsi_assemble_batched", "nsi_assemble_vjp", "nsi_assemble_host",
-    "nsi_assemble_convective", "nsi_assemble_nodal",
+    "nsi_assemble_convective", "nsi_assemble_nodal", "nsi_assemble_stabilized",
     "nsi_residual", "nsi_device_status", "nsi_set_timing_events", "nsi_autotune", "nsi_set_launch",
     "nsi_last_error", "nsi_abi_version",
     "Assembler", "NsiResidual", "assemble_batched",
@@ -78,7 +78,7 @@ class NsiInfo(ctypes.Structure):
                 ("n_colors", ctypes.c_int32), ("max_row", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("scatter", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("rows_per_block", ctypes.c_int32),
                 ("n_plans", ctypes.c_int32), ("persistent", ctypes.c_int32), ("exact_rows", ctypes.c_int32),
-                ("long_rows", ctypes.c_int32)]
+                ("long_rows", ctypes.c_int32), ("fan_ok", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -95,6 +95,7 @@ _SIGNATURES = {
     "nsi_assemble_vjp": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
     "nsi_assemble_convective": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
     "nsi_assemble_nodal": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
+    "nsi_assemble_stabilized": [_P, ctypes.POINTER(NsiFields), _P, _P, _P, _P],
     "nsi_assemble_host": [_P, ctypes.POINTER(NsiFields), ctypes.POINTER(NsiOutputs), _P],
     "nsi_residual": [_P, ctypes.POINTER(NsiFields), _P, _P],
     "nsi_device_status": [_P, _P],
@@ -207,6 +208,10 @@ def nsi_assemble_convective(h, fields: NsiFields, A_static_ptr, A_ptr, rhs_ptr, 
 
 def nsi_assemble_nodal(h, fields: NsiFields, rhs_ptr, dt_rho_ptr, mass_rho_ptr, stream=None):
     _check(load_library().nsi_assemble_nodal(h, ctypes.byref(fields), rhs_ptr, dt_rho_ptr, mass_rho_ptr, stream))
+
+
+def nsi_assemble_stabilized(h, fields: NsiFields, Auu_ptr, G_ptr, rhs_ptr, stream=None):
+    _check(load_library().nsi_assemble_stabilized(h, ctypes.byref(fields), Auu_ptr, G_ptr, rhs_ptr, stream))
 
 
 def nsi_assemble_host(h, fields: NsiFields, outputs: NsiOutputs, stream=None):
@@ -377,6 +382,22 @@ class Assembler:
             raise ValueError("A_static must be a contiguous [nnz] tensor of the output dtype")
         nsi_assemble_convective(self.handle, f, _ptr(A_static), _ptr(A), _ptr(rhs), _stream_ptr(stream))
         return A, rhs
+
+    def assemble_stabilized(self, u, u_n=None, rho=1.0, mu=1e-3, dt=1e-2, out=None, stream=None):
+        """(Auu [9, nnz], G [3, nnz], rhs [3, n]): the stabilised velocity block,
+        Auu[3 i + j] the (i, j) entry of every CSR entry's 3x3 block."""
+        torch = _torch()
+        f, keep = self.fields(u, u_n, rho, mu, dt)
+        if out is None:
+            out = (torch.empty(9, self.nnz, dtype=self.out_dtype, device=self.device),
+                   torch.empty(3, self.nnz, dtype=self.out_dtype, device=self.device),
+                   torch.empty(3, self.n, dtype=self.out_dtype, device=self.device))
+        Auu, G, rhs = out
+        for t, shape in ((Auu, (9, self.nnz)), (G, (3, self.nnz)), (rhs, (3, self.n))):
+            if t.dtype != self.out_dtype or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"stabilised output must be a contiguous {shape} tensor of the output dtype")
+        nsi_assemble_stabilized(self.handle, f, _ptr(Auu), _ptr(G), _ptr(rhs), _stream_ptr(stream))
+        return Auu, G, rhs
 
     def nodal(self, u_n, rho=1.0, dt=1e-2, out=None, stream=None):
         """(rhs [3, n], dt_rho [n], mass_rho [n]): the paper's per-node outputs."""

@@ -75,6 +75,8 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->long_inc);
   cudaFree(h->exact_ptr);
   cudaFree(h->exact_inc);
+  cudaFree(h->star_ptr);
+  cudaFree(h->star_inc);
   cudaFree(h->fan);
   cudaFree(h->fan_blk);
   cudaFree(h->xyz64);
@@ -746,6 +748,16 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->exact_ptr, exact_ptr.data(), exact_ptr.size(), s))) return st;
     if ((st = dev_upload(h, &h->exact_inc, exact_inc.data(), exact_inc.size(), s))) return st;
   }
+  // the stabilised block's per-row kernel needs every row's elements when
+  // there is no fan map (host copies kept until the uploads have completed)
+  std::vector<int32_t> star_ptr_h;
+  std::vector<uint32_t> star_inc_h;
+  if (!h->fan_ok && E <= (int64_t)(UINT32_MAX >> 2) && inc_ptr[n] <= INT32_MAX) {
+    star_ptr_h.assign(inc_ptr.begin(), inc_ptr.end());
+    star_inc_h.assign(inc.begin(), inc.end());
+    if ((st = dev_upload(h, &h->star_ptr, star_ptr_h.data(), star_ptr_h.size(), s))) return st;
+    if ((st = dev_upload(h, &h->star_inc, star_inc_h.data(), star_inc_h.size(), s))) return st;
+  }
   if (h->precision == NSI_FP64) {
     if ((st = dev_upload(h, &h->xyz64, xyz64.data(), n, s))) return st;
   } else {
@@ -862,6 +874,7 @@ nsi_status nsi_info(const NsiHandle* h, NsiInfo* info) {
   info->persistent = h->persistent && !h->use_fan ? 1 : 0;
   info->exact_rows = (int32_t)std::min<int64_t>(h->exact_rows, INT32_MAX);
   info->long_rows = (int32_t)std::min<int64_t>(h->long_rows, INT32_MAX);
+  info->fan_ok = h->fan_ok ? 1 : 0;
   return NSI_OK;
 }
 

@@ -191,6 +191,10 @@ struct NsiHandle {
   int32_t* exact_list = nullptr;  // [exact_rows] their node ids
   int32_t* exact_ptr = nullptr;   // [exact_rows + 1] into exact_inc
   uint32_t* exact_inc = nullptr;  // element * 4 + local index of the row's node
+  // meshes without an edge-fan map: every row's incident elements, for the
+  // stabilised block's per-row kernel (null when the fan map exists)
+  int32_t* star_ptr = nullptr;   // [n + 1] into star_inc
+  uint32_t* star_inc = nullptr;  // element * 4 + local index of the row's node
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
   int n_plans = 0;

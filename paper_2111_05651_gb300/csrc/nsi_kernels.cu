@@ -1830,34 +1830,45 @@ __device__ __forceinline__ Acc<P> acc_scale(const Acc<P>& a, typename Prec<P>::T
   return r;
 }
 
-template <int P, bool DEBUG>
-__device__ __forceinline__ void fan_block(const MeshView& m, const FieldView& f, const OutView& o, int64_t blk,
-                                          unsigned char* smem) {
-  using T = typename Prec<P>::T;
-  using Out = typename Prec<P>::Out;
-  constexpr int TB = FAN_BLOCK;
-  T4<T>* rec0 = reinterpret_cast<T4<T>*>(smem + FanSmem<P>::rec());
-  T4<T>* rec1 = rec0 + TB;
-  int32_t* rp = reinterpret_cast<int32_t*>(smem + FanSmem<P>::rp(TB));
-  Acc<P>* red = reinterpret_cast<Acc<P>*>(smem + FanSmem<P>::red(TB));  // 5 arrays of TB
-  const int k = threadIdx.x;
-  const int64_t R0 = m.fan_blk[blk], R1 = m.fan_blk[blk + 1];
-  const int nr = (int)(R1 - R0);
-  const int32_t base = m.row_ptr[R0];
-  const int L = m.row_ptr[R1] - base;
-  if (DEBUG && (L > TB || nr > TB)) {
-    if (k == 0) atomicOr(m.err, ERR_STAR);
-    return;
-  }
-  const T kc = kc_of<T>(f), kmu = kmu_of<T>(f), kmass = kmass_of<T>(f);
-  const T kg = (T)(-1.0 / 24.0);
+// One CSR entry of a fan block (blocks of whole rows, one thread per entry):
+// its row within the block, the row's start and length in the block, the
+// diagonal's position, the fan word, and (node i the row's node, j the
+// column's) the edge vector d_j = x_j - x_i and the velocities u_j, u_i.
+template <typename T>
+struct FanEntry {
+  int64_t R0;
+  int32_t base;
+  int nr, L, row, a, len, dp;
+  uint32_t w;
+  V3<T> dj, uj, ui;
+};
 
-  // 1. row starts of the block; this entry's neighbour record (calculate_transients)
-  for (int r = k; r <= nr; r += TB) rp[r] = m.row_ptr[R0 + r] - base;
-  uint32_t w = 0;
-  if (k < L) {
-    const int j = m.col_idx[base + k];
-    w = m.fan[base + k];
+// Steps 1-2 of a fan block: the row starts of the block, this entry's
+// neighbour record (calculate_transients), its row and edge vector; then
+// every entry's record in shared memory is replaced by (edge vector from its
+// row's node, velocity).  Returns false (block-uniform) when DEBUG finds the
+// block larger than the kernel's.
+template <int P, bool DEBUG>
+__device__ __forceinline__ bool fan_entry(const MeshView& m, int64_t blk, T4<typename Prec<P>::T>* rec0,
+                                          T4<typename Prec<P>::T>* rec1, int32_t* rp,
+                                          FanEntry<typename Prec<P>::T>& e) {
+  using T = typename Prec<P>::T;
+  constexpr int TB = FAN_BLOCK;
+  const int k = threadIdx.x;
+  e.R0 = m.fan_blk[blk];
+  const int64_t R1 = m.fan_blk[blk + 1];
+  e.nr = (int)(R1 - e.R0);
+  e.base = m.row_ptr[e.R0];
+  e.L = m.row_ptr[R1] - e.base;
+  if (DEBUG && (e.L > TB || e.nr > TB)) {
+    if (k == 0) atomicOr(m.err, ERR_STAR);
+    return false;
+  }
+  for (int r = k; r <= e.nr; r += TB) rp[r] = m.row_ptr[e.R0 + r] - e.base;
+  e.w = 0;
+  if (k < e.L) {
+    const int j = m.col_idx[e.base + k];
+    e.w = m.fan[e.base + k];
     if (!DEBUG || (j >= 0 && j < m.n)) {
       const unsigned char* r = static_cast<const unsigned char*>(m.rec) + (size_t)j * (2 * sizeof(T4<T>));
       if constexpr (P == NSI_FP64) {
@@ -1876,39 +1887,61 @@ __device__ __forceinline__ void fan_block(const MeshView& m, const FieldView& f,
   cp_async_wait_all();
   __syncthreads();
 
-  // 2. this entry's row, and its edge vector from the row's own node
-  int row = 0, a = 0, len = 0, dp = 0;
-  V3<T> dj{T(0), T(0), T(0)}, uj{T(0), T(0), T(0)}, ui{T(0), T(0), T(0)};
-  if (k < L) {
-    int lo = 0, hi = nr - 1;  // last row whose start is <= k
+  e.row = e.a = e.len = e.dp = 0;
+  e.dj = e.uj = e.ui = V3<T>{T(0), T(0), T(0)};
+  if (k < e.L) {
+    int lo = 0, hi = e.nr - 1;  // last row whose start is <= k
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (rp[mid] <= k) lo = mid;
       else hi = mid - 1;
     }
-    row = lo;
-    a = rp[row];
-    len = rp[row + 1] - a;
-    dp = m.diag_pos[R0 + row];
+    e.row = lo;
+    e.a = rp[e.row];
+    e.len = rp[e.row + 1] - e.a;
+    e.dp = m.diag_pos[e.R0 + e.row];
     const T4<T> h = rec0[k], s = rec1[k];
-    const T4<T> hd = rec0[a + dp], sd = rec1[a + dp];
+    const T4<T> hd = rec0[e.a + e.dp], sd = rec1[e.a + e.dp];
     if constexpr (P == NSI_FP64) {
-      dj = {h.x - hd.x, h.y - hd.y, h.z - hd.z};
-      uj = {s.x, s.y, s.z};
-      ui = {sd.x, sd.y, sd.z};
+      e.dj = {h.x - hd.x, h.y - hd.y, h.z - hd.z};
+      e.uj = {s.x, s.y, s.z};
+      e.ui = {sd.x, sd.y, sd.z};
     } else {
       const V3<float> lj = record_lo(s.z, s.w), li = record_lo(sd.z, sd.w);
-      dj = add(sub(V3<float>{h.x, h.y, h.z}, V3<float>{hd.x, hd.y, hd.z}), sub(lj, li));
-      uj = {h.w, s.x, s.y};
-      ui = {hd.w, sd.x, sd.y};
+      e.dj = add(sub(V3<float>{h.x, h.y, h.z}, V3<float>{hd.x, hd.y, hd.z}), sub(lj, li));
+      e.uj = {h.w, s.x, s.y};
+      e.ui = {hd.w, sd.x, sd.y};
     }
   }
   __syncthreads();
-  if (k < L) {
-    rec0[k] = T4<T>{dj.x, dj.y, dj.z, T(0)};
-    rec1[k] = T4<T>{uj.x, uj.y, uj.z, T(0)};
+  if (k < e.L) {
+    rec0[k] = T4<T>{e.dj.x, e.dj.y, e.dj.z, T(0)};
+    rec1[k] = T4<T>{e.uj.x, e.uj.y, e.uj.z, T(0)};
   }
   __syncthreads();
+  return true;
+}
+
+template <int P, bool DEBUG>
+__device__ __forceinline__ void fan_block(const MeshView& m, const FieldView& f, const OutView& o, int64_t blk,
+                                          unsigned char* smem) {
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  constexpr int TB = FAN_BLOCK;
+  T4<T>* rec0 = reinterpret_cast<T4<T>*>(smem + FanSmem<P>::rec());
+  T4<T>* rec1 = rec0 + TB;
+  int32_t* rp = reinterpret_cast<int32_t*>(smem + FanSmem<P>::rp(TB));
+  Acc<P>* red = reinterpret_cast<Acc<P>*>(smem + FanSmem<P>::red(TB));  // 5 arrays of TB
+  const int k = threadIdx.x;
+  FanEntry<T> fe;
+  if (!fan_entry<P, DEBUG>(m, blk, rec0, rec1, rp, fe)) return;
+  const int64_t R0 = fe.R0;
+  const int nr = fe.nr, L = fe.L, row = fe.row, a = fe.a, len = fe.len, dp = fe.dp;
+  const int32_t base = fe.base;
+  const uint32_t w = fe.w;
+  const V3<T> dj = fe.dj, uj = fe.uj, ui = fe.ui;
+  const T kc = kc_of<T>(f), kmu = kmu_of<T>(f), kmass = kmass_of<T>(f);
+  const T kg = (T)(-1.0 / 24.0);
 
   // 3. the fan of an off-diagonal entry, summed in registers
   Acc<P> sA, sGx, sGy, sGz, sD;
@@ -2030,6 +2063,367 @@ template <int P, bool DEBUG>
 __global__ void __launch_bounds__(FAN_BLOCK) fan_kernel(MeshView m, FieldView f, OutView o) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fan_block<P, DEBUG>(m, f, o, blockIdx.x, smem_raw);
+}
+
+// --------------------------------------------- stabilised velocity block ---
+// The paper's 12x12 element matrix (Section II-A: every pair of dimensions of
+// two nodes coupled, equal dimensions receiving the scalar part) assembled on
+// the CSR pattern as one 3x3 block per entry, Auu[(3 a + b) nnz + p] the
+// (a, b) entry of the block of entry p = (i, j):
+//   Auu(i,j)[a][b] = delta_ab (A(i,j) + S(i,j)) + K(i,j)[a][b]
+// with A the Galerkin operator and the implicit terms of Codina's algebraic
+// subgrid scales (Comput. Methods Appl. Mech. Engrg. 191 (2002) 4295-4321,
+// linear elements, c1 = 4, c2 = 2):
+//   tau1 = (4 mu / h^2 + 2 rho |ubar| / h)^-1,  tau2 = h^2 / (4 tau1),
+//   S(i,j)       += tau1 rho^2 int (u . grad N_i)(u . grad N_j)
+//   K(i,j)[a][b] += mu int d_b N_i d_a N_j + tau2 int d_a N_i d_b N_j
+// per element, h = (6 |T|)^(1/3) = det^(1/3), ubar the mean of the element's
+// four node velocities.  With the cofactors c_n = det grad N_n, the sum us of
+// the four velocities and s = |us| (so 2 rho |ubar| h = rho s h / 2, and the
+// moments int lam_m lam_n = |T| (1 + delta_mn) / 20 of the linear velocity):
+//   S += rho^2 / (120 h (4 mu + rho s h / 2)) [(us . c_i)(us . c_j) + sum_n (u_n . c_i)(u_n . c_j)]
+//   K[a][b] += kv c_j[a] c_i[b] + kd c_i[a] c_j[b],
+//   kv = mu / (6 det),  kd = tau2 / (6 det) = kv + rho s h / (48 det).
+// Every term vanishes on a constant column field (sum_n c_n = 0), so, as for
+// A, the diagonal block is the lumped mass times I minus the sum of the row's
+// off-diagonal blocks.
+struct StabConst {
+  double ks, k4mu, krh, kr48;  // rho^2 / 120, 4 mu, rho / 2, rho / 48
+  float ksf, k4muf, krhf, kr48f;
+};
+
+static StabConst stab_const(const NsiFields* f) {
+  StabConst c;
+  c.ks = f->rho * f->rho / 120.0;
+  c.k4mu = 4.0 * f->mu;
+  c.krh = f->rho / 2.0;
+  c.kr48 = f->rho / 48.0;
+  c.ksf = (float)c.ks;
+  c.k4muf = (float)c.k4mu;
+  c.krhf = (float)c.krh;
+  c.kr48f = (float)c.kr48;
+  return c;
+}
+
+template <typename T>
+struct StabK {
+  T ks, k4mu, krh, kr48;
+};
+template <typename T>
+__device__ __forceinline__ StabK<T> stab_k(const StabConst& c) {
+  if constexpr (sizeof(T) == 8) return StabK<T>{c.ks, c.k4mu, c.krh, c.kr48};
+  else return StabK<T>{c.ksf, c.k4muf, c.krhf, c.kr48f};
+}
+__device__ __forceinline__ float cbrt_of(float x) { return cbrtf(x); }
+__device__ __forceinline__ double cbrt_of(double x) { return cbrt(x); }
+__device__ __forceinline__ float sqrt_of(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_of(double x) { return sqrt(x); }
+__device__ __forceinline__ float fma_of(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_of(double a, double b, double c) { return fma(a, b, c); }
+
+// One element's stabilisation terms for the entry (row node, column node):
+// ci, cj the two nodes' cofactors, det, and the element's four node
+// velocities (any order).  K is added to; S is returned.
+template <typename T>
+__device__ __forceinline__ T stab_terms(const V3<T>& ci, const V3<T>& cj, T det, const V3<T>& ua, const V3<T>& ub,
+                                        const V3<T>& uc, const V3<T>& ud, const StabK<T>& k, T kmu, T (&K)[9]) {
+  const V3<T> us = add(add(ua, ub), add(uc, ud));
+  const T h = cbrt_of(det);
+  const T sh = sqrt_of(dot(us, us)) * h;  // s h
+  const T rdet = rcp_fast(det);
+  T mm = dot(us, ci) * dot(us, cj);
+  mm = fma_of(dot(ua, ci), dot(ua, cj), mm);
+  mm = fma_of(dot(ub, ci), dot(ub, cj), mm);
+  mm = fma_of(dot(uc, ci), dot(uc, cj), mm);
+  mm = fma_of(dot(ud, ci), dot(ud, cj), mm);
+  const T kv = kmu * rdet;
+  const T kd = fma_of(k.kr48 * sh, rdet, kv);
+  const T r[3] = {ci.x, ci.y, ci.z}, c[3] = {cj.x, cj.y, cj.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) K[3 * a + b] = fma_of(kv * c[a], r[b], fma_of(kd * r[a], c[b], K[3 * a + b]));
+  return k.ks * mm * rcp_fast(h * fma_of(k.krh, sh, k.k4mu));
+}
+
+// shared memory of a stabilised fan block (T entries): the records, the row
+// starts, the A + S and lumped-mass accumulators, and twelve arrays of plain
+// sums (K's nine components, then G's three)
+template <int P>
+struct StabFanSmem {
+  using T = typename Prec<P>::T;
+  static constexpr size_t rp(int Tn) { return 2 * sizeof(T4<T>) * (size_t)Tn; }
+  static constexpr size_t red(int Tn) { return rp(Tn) + (((size_t)4 * (Tn + 1) + 15) & ~size_t(15)); }
+  static constexpr size_t vals(int Tn) { return red(Tn) + 2 * sizeof(Acc<P>) * (size_t)Tn; }
+  static constexpr size_t total(int Tn) { return vals(Tn) + 12 * sizeof(T) * (size_t)Tn; }
+};
+
+// The stabilised block by edge fans: one thread per CSR entry (i, j) of a
+// block of whole rows, as fan_block.  An off-diagonal entry sums over the
+// elements (i, j, k_m, k_m+1) around its edge, in registers: A + S (one
+// accumulator, compensated in mixed64), K's nine components and G's three
+// (plain sums of at most seven elements), det for the lumped mass.  The row
+// totals reach the diagonal through a tree reduction in shared memory.  Every
+// output is written once, coalesced across the block: Auu component-major,
+// then G and the right-hand side as the Galerkin assembly.
+template <int P, bool DEBUG>
+__global__ void __launch_bounds__(FAN_BLOCK) stab_fan_kernel(MeshView m, FieldView f, StabConst sc, void* Auu,
+                                                             void* Gv, void* rhs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using T = typename Prec<P>::T;
+  using Out = typename Prec<P>::Out;
+  constexpr int TB = FAN_BLOCK;
+  T4<T>* rec0 = reinterpret_cast<T4<T>*>(smem);
+  T4<T>* rec1 = rec0 + TB;
+  int32_t* rp = reinterpret_cast<int32_t*>(smem + StabFanSmem<P>::rp(TB));
+  Acc<P>* rA = reinterpret_cast<Acc<P>*>(smem + StabFanSmem<P>::red(TB));
+  Acc<P>* rD = rA + TB;
+  T* rv = reinterpret_cast<T*>(smem + StabFanSmem<P>::vals(TB));
+  const int k = threadIdx.x;
+  FanEntry<T> fe;
+  if (!fan_entry<P, DEBUG>(m, blockIdx.x, rec0, rec1, rp, fe)) return;
+  const T kc = kc_of<T>(f), kmu = kmu_of<T>(f), kmass = kmass_of<T>(f);
+  const StabK<T> sk = stab_k<T>(sc);
+  const T kg = (T)(-1.0 / 24.0);
+
+  Acc<P> sA, sD;
+  sA.zero();
+  sD.zero();
+  T sK[9], sG[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int c = 0; c < 9; ++c) sK[c] = T(0);
+  const int nring = (fe.w >> 24) & 7;
+  if (k < fe.L && nring > 0) {
+    const bool closed = (fe.w >> 27) & 1;
+    const int nel = closed ? nring : nring - 1;
+    const V3<T> dj = fe.dj, uj = fe.uj, ui = fe.ui;
+    const V3<T> uij{ui.x + ui.x + uj.x, ui.y + ui.y + uj.y, ui.z + ui.z + uj.z};  // 2 u_i + u_j
+    auto node = [&](int mpos, V3<T>& d, V3<T>& u) {
+      const int pos = (fe.w >> (4 * mpos)) & 15;
+      if (DEBUG && pos >= fe.len) atomicOr(m.err, ERR_STAR);
+      const T4<T> x = rec0[fe.a + pos], y = rec1[fe.a + pos];
+      d = {x.x, x.y, x.z};
+      u = {y.x, y.y, y.z};
+    };
+    V3<T> d0, u0;
+    node(0, d0, u0);
+    V3<T> q0 = cross(dj, d0);
+    const V3<T> dfirst = d0, ufirst = u0, qfirst = q0;
+    for (int e = 0; e < nel; ++e) {
+      V3<T> d1, u1, q1;
+      if (e + 1 < nring) {
+        node(e + 1, d1, u1);
+        q1 = cross(dj, d1);
+      } else {  // closing element of an interior ring
+        d1 = dfirst;
+        u1 = ufirst;
+        q1 = qfirst;
+      }
+      const V3<T> cj = cross(d0, d1);
+      const T det = dot(dj, cj);
+      const V3<T> ci{-(cj.x + q0.x - q1.x), -(cj.y + q0.y - q1.y), -(cj.z + q0.z - q1.z)};
+      const T kv = kmu * rcp_fast(det);
+      const V3<T> w3{kc * (uij.x + u0.x + u1.x) + kv * ci.x, kc * (uij.y + u0.y + u1.y) + kv * ci.y,
+                     kc * (uij.z + u0.z + u1.z) + kv * ci.z};
+      const T st = stab_terms<T>(ci, cj, det, ui, uj, u0, u1, sk, kmu, sK);
+      sA.add(dot(w3, cj) + st);
+      sG[0] += ci.x;
+      sG[1] += ci.y;
+      sG[2] += ci.z;
+      sD.add(det);
+      d0 = d1;
+      u0 = u1;
+      q0 = q1;
+    }
+  }
+
+  // row totals for the diagonal block
+  if (k < fe.L) {
+    rA[k] = sA;
+    rD[k] = sD;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) rv[c * TB + k] = sK[c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rv[(9 + d) * TB + k] = sG[d];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int st = 1; st < FAN_MAX_ROW; st <<= 1) {
+    if (k < fe.L && ((k - fe.a) & (2 * st - 1)) == 0 && k - fe.a + st < fe.len) {
+      acc_merge<P>(rA[k], rA[k + st]);
+      acc_merge<P>(rD[k], rD[k + st]);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) rv[c * TB + k] += rv[c * TB + k + st];
+    }
+    __syncthreads();
+  }
+
+  Out* A = static_cast<Out*>(Auu);
+  Out* G = static_cast<Out*>(Gv);
+  Out* Rh = static_cast<Out*>(rhs);
+  if (k < fe.L) {
+    const int64_t g = (int64_t)fe.base + k;
+    if (k == fe.a + fe.dp) {
+      const Acc<P> mass = acc_scale<P>(acc_third<P>(rD[fe.a]), kmass);
+      Acc<P> dA = mass;
+      if constexpr (P == NSI_MIXED_F32_ACC64) {
+        dA.add(-rA[fe.a].hi);
+        dA.lo -= rA[fe.a].lo;
+      } else {
+        dA.v = mass.v - rA[fe.a].v;
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const T kt = -rv[c * TB + fe.a];
+        if (c % 4 == 0) {
+          Acc<P> t = dA;
+          t.add(kt);
+          store_acc(A + c * m.nnz + g, t);
+        } else {
+          A[c * m.nnz + g] = (Out)kt;
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) G[d * m.nnz + g] = (Out)(rv[(9 + d) * TB + fe.a] * (kg / T(3)));
+      const int64_t i = fe.R0 + fe.row;
+      const V3<T> un = load_vec<T>(f.un, i);
+      store_acc(Rh + i, acc_scale<P>(mass, un.x));
+      store_acc(Rh + m.n + i, acc_scale<P>(mass, un.y));
+      store_acc(Rh + 2 * m.n + i, acc_scale<P>(mass, un.z));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        if (c % 4 == 0) {
+          Acc<P> t = sA;
+          t.add(sK[c]);
+          store_acc(A + c * m.nnz + g, t);
+        } else {
+          A[c * m.nnz + g] = (Out)sK[c];
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) G[d * m.nnz + g] = (Out)(sG[d] * kg);
+    }
+  }
+  // rows without entries (nodes in no element): zero right-hand side
+  for (int r = k; r < fe.nr; r += TB) {
+    if (rp[r + 1] == rp[r]) {
+      Rh[fe.R0 + r] = Out(0);
+      Rh[m.n + fe.R0 + r] = Out(0);
+      Rh[2 * m.n + fe.R0 + r] = Out(0);
+    }
+  }
+}
+
+// The stabilised block of listed rows (or of every row when `rows` is null),
+// one thread per row in double whatever the handle's precision: the mixed
+// modes' rows touching badly shaped elements, and whole meshes without an
+// edge-fan map.  Each off-diagonal entry (i, j) sums the row's elements that
+// contain j (node i first, the others in an even order so that det > 0), the
+// diagonal block follows from the row totals as in the fan kernel.
+template <int P>
+__global__ void __launch_bounds__(64) stab_rows_kernel(MeshView m, FieldView f, StabConst sc, void* Auu, void* Gv,
+                                                       void* rhs, const int32_t* rows, const int32_t* ptr,
+                                                       const uint32_t* inc, int64_t count) {
+  using Out = typename Prec<P>::Out;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const int64_t i = rows ? rows[r] : r;
+  const int32_t rs = m.row_ptr[i], len = m.row_ptr[i + 1] - rs;
+  const int32_t* cols = m.col_idx + rs;
+  auto coord = [&](int64_t j) {
+    if constexpr (P == NSI_FP64) {
+      const D4 x = m.xyz64[j];
+      return V3<double>{x.x, x.y, x.z};
+    } else {
+      const float4 h = m.xyz_hi[j], l = m.xyz_lo[j];
+      return V3<double>{(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+    }
+  };
+  auto vel = [&](const void* const* comp, int64_t j) {
+    if constexpr (P == NSI_FP64) return load_vec<double>(comp, j);
+    else {
+      const V3<float> w = load_vec<float>(comp, j);
+      return V3<double>{w.x, w.y, w.z};
+    }
+  };
+  const int EVEN[4][3] = {{1, 2, 3}, {0, 3, 2}, {3, 0, 1}, {2, 1, 0}};
+  const V3<double> xi = coord(i), ui = vel(f.u, i);
+  const StabK<double> sk = stab_k<double>(sc);
+  struct El {
+    int v[3];
+    V3<double> c[3], ci, u[3];
+    double det;
+  };
+  auto element = [&](int32_t t) {
+    El el;
+    const int64_t e = inc[t] >> 2;
+    const int a = (int)(inc[t] & 3u);
+    const int4 v4 = m.lnods[e];
+    const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+    V3<double> d[3];
+    for (int b = 0; b < 3; ++b) {
+      el.v[b] = v[EVEN[a][b]];
+      d[b] = sub(coord(el.v[b]), xi);
+      el.u[b] = vel(f.u, el.v[b]);
+    }
+    el.c[0] = cross(d[1], d[2]);
+    el.c[1] = cross(d[2], d[0]);
+    el.c[2] = cross(d[0], d[1]);
+    el.det = dot(d[0], el.c[0]);
+    el.ci = V3<double>{-(el.c[0].x + el.c[1].x + el.c[2].x), -(el.c[0].y + el.c[1].y + el.c[2].y),
+                       -(el.c[0].z + el.c[1].z + el.c[2].z)};
+    return el;
+  };
+  double detsum = 0.0;
+  for (int32_t t = ptr[r]; t < ptr[r + 1]; ++t) detsum += element(t).det;
+  Out* A = static_cast<Out*>(Auu) + rs;
+  Out* G = static_cast<Out*>(Gv) + rs;
+  double sa = 0.0, sK[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, sg[3] = {0.0, 0.0, 0.0};
+  int dpos = -1;
+  for (int q = 0; q < len; ++q) {
+    const int32_t j = cols[q];
+    if (j == i) {
+      dpos = q;
+      continue;
+    }
+    double a = 0.0, K[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, g[3] = {0.0, 0.0, 0.0};
+    for (int32_t t = ptr[r]; t < ptr[r + 1]; ++t) {
+      const int4 v4 = m.lnods[inc[t] >> 2];
+      if (v4.x != j && v4.y != j && v4.z != j && v4.w != j) continue;
+      const El el = element(t);
+      const int b = el.v[0] == j ? 0 : el.v[1] == j ? 1 : 2;
+      const double kv = f.kmu / el.det;
+      const V3<double> us2{2.0 * ui.x + el.u[0].x + el.u[1].x + el.u[2].x,
+                           2.0 * ui.y + el.u[0].y + el.u[1].y + el.u[2].y,
+                           2.0 * ui.z + el.u[0].z + el.u[1].z + el.u[2].z};
+      const V3<double> w{f.kc * us2.x + kv * el.ci.x, f.kc * us2.y + kv * el.ci.y, f.kc * us2.z + kv * el.ci.z};
+      a += dot(w, el.c[b]);
+      a += stab_terms<double>(el.ci, el.c[b], el.det, ui, el.u[0], el.u[1], el.u[2], sk, f.kmu, K);
+      g[0] += el.ci.x;
+      g[1] += el.ci.y;
+      g[2] += el.ci.z;
+    }
+    sa += a;
+    for (int c = 0; c < 9; ++c) {
+      sK[c] += K[c];
+      A[c * m.nnz + q] = (Out)((c % 4 == 0 ? a : 0.0) + K[c]);
+    }
+    for (int d = 0; d < 3; ++d) {
+      G[d * m.nnz + q] = (Out)(-g[d] / 24.0);
+      sg[d] += g[d];
+    }
+  }
+  if (dpos >= 0) {
+    const double dm = f.kmass * detsum - sa;
+    for (int c = 0; c < 9; ++c) A[c * m.nnz + dpos] = (Out)((c % 4 == 0 ? dm : 0.0) - sK[c]);
+    for (int d = 0; d < 3; ++d) G[d * m.nnz + dpos] = (Out)(-sg[d] / 72.0);
+  }
+  const V3<double> un = vel(f.un, i);
+  Out* Rh = static_cast<Out*>(rhs);
+  Rh[i] = (Out)(f.kmass * detsum * un.x);
+  Rh[m.n + i] = (Out)(f.kmass * detsum * un.y);
+  Rh[2 * m.n + i] = (Out)(f.kmass * detsum * un.z);
 }
 
 template <int P, bool DEBUG>
@@ -2944,6 +3338,35 @@ static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOut
   return NSI_OK;
 }
 
+// the stabilised velocity block: pack and the fan kernel (then, in the mixed
+// modes, the rows touching badly shaped elements in double), or the per-row
+// kernel over every row when the mesh has no fan map
+static_assert(StabFanSmem<NSI_FP64>::total(FAN_BLOCK) <= 48 * 1024, "stabilised fan block above 48 KB");
+template <int P>
+static nsi_status stabilized_p(NsiHandle* h, const FieldView& f, const StabConst& sc, void* Auu, void* G, void* rhs,
+                               cudaStream_t s) {
+  if (h->n == 0) return NSI_OK;
+  MeshView m = view_of(h);
+  if (h->fan_ok) {
+    const size_t smem = StabFanSmem<P>::total(FAN_BLOCK);
+    pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
+    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
+    if (h->debug) stab_fan_kernel<P, true><<<h->fan_blocks, FAN_BLOCK, smem, s>>>(m, f, sc, Auu, G, rhs);
+    else stab_fan_kernel<P, false><<<h->fan_blocks, FAN_BLOCK, smem, s>>>(m, f, sc, Auu, G, rhs);
+    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
+    nsi_status st = check_launch("stab_fan_kernel");
+    if (st || P == NSI_FP64 || h->exact_rows == 0) return st;
+    stab_rows_kernel<P><<<(h->exact_rows + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, h->exact_list, h->exact_ptr,
+                                                                  h->exact_inc, h->exact_rows);
+    return check_launch("stab_rows_kernel (exact rows)");
+  }
+  if (!h->star_ptr) return fail(NSI_ERR_UNSUPPORTED, "no row incidence for the stabilised block of this mesh");
+  if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
+  stab_rows_kernel<P><<<(h->n + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, nullptr, h->star_ptr, h->star_inc, h->n);
+  if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
+  return check_launch("stab_rows_kernel");
+}
+
 extern "C" {
 
 nsi_status nsi_assemble(NsiHandle* h, const NsiFields* f, const NsiOutputs* o, void* stream) {
@@ -2982,6 +3405,28 @@ nsi_status nsi_assemble_convective(NsiHandle* h, const NsiFields* f, const void*
   if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");
   const StepView o{A_static, A_val, rhs, nullptr, nullptr, 0.0, 0.0f};
   return step_dispatch(h, f, o, false, static_cast<cudaStream_t>(stream));
+}
+
+nsi_status nsi_assemble_stabilized(NsiHandle* h, const NsiFields* f, void* Auu, void* G_val, void* rhs,
+                                   void* stream) {
+  if (!h || !f || !rhs || (h->nnz > 0 && (!Auu || !G_val))) return fail(NSI_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < 3; ++k)
+    if (!f->u[k]) return fail(NSI_ERR_INVALID_ARG, "velocity component pointer is NULL");
+  if (!(f->dt > 0.0)) return fail(NSI_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(f->mu > 0.0) || !std::isfinite(f->mu))
+    return fail(NSI_ERR_INVALID_ARG, "mu must be finite and > 0 (tau1 of an element at rest is h^2 / (4 mu))");
+  if (!(f->rho >= 0.0) || !std::isfinite(f->rho)) return fail(NSI_ERR_INVALID_ARG, "rho must be finite and >= 0");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return fail(NSI_ERR_INVALID_ARG, "current device differs from the handle's device");
+  const FieldView fv = fields_of(f);
+  const StabConst sc = stab_const(f);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (h->precision) {
+    case NSI_FP64: return stabilized_p<NSI_FP64>(h, fv, sc, Auu, G_val, rhs, s);
+    case NSI_MIXED_F32_ACC64: return stabilized_p<NSI_MIXED_F32_ACC64>(h, fv, sc, Auu, G_val, rhs, s);
+    default: return stabilized_p<NSI_MIXED_F32_ACC32>(h, fv, sc, Auu, G_val, rhs, s);
+  }
 }
 
 nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void* dt_rho, void* mass_rho, void* stream) {

@@ -95,6 +95,7 @@ def test_calls_on_null_handle():
     assert lib.nsi_assemble_noalloc(None, ctypes.byref(f), ctypes.byref(o), None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_assemble_convective(None, ctypes.byref(f), None, None, None, None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_assemble_nodal(None, ctypes.byref(f), None, None, None, None) == nsi.NSI_ERR_INVALID_ARG
+    assert lib.nsi_assemble_stabilized(None, ctypes.byref(f), None, None, None, None) == nsi.NSI_ERR_INVALID_ARG
     assert lib.nsi_assemble_destroy(None) == nsi.NSI_OK
     hs = (ctypes.c_void_p * 1)()
     assert lib.nsi_assemble_batched(hs, None, None, -1, None) == nsi.NSI_ERR_INVALID_ARG
