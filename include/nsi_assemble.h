@@ -192,8 +192,7 @@ typedef struct {
                                of the mesh stays on the row gather */
     int32_t fan_ok;         /* 1: the mesh has an edge-fan map (rows of at most 16 entries, the
                                ring of elements around every edge at most 7 nodes, no long
-                               rows): the edge-fan kernel and the stabilised block's fan kernel
-                               are available */
+                               rows): the edge-fan kernel is available (nsi_set_launch) */
 } NsiInfo;
 nsi_status nsi_info(const NsiHandle* h, NsiInfo* info);
 
@@ -276,12 +275,15 @@ nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void*
  *                   of every CSR entry (row node's dimension i, column
  *                   node's dimension j);
  *   G_val [3][nnz] and rhs [3][n_nodes]: as nsi_assemble.
- * Meshes with an edge-fan map (NsiInfo.fan_ok) run one thread per CSR entry;
- * the mixed modes then recompute the rows touching badly shaped elements in
- * double.  Other meshes run one double-precision thread per row.  Precision
- * as nsi_assemble; in NSI_MIXED_F32_ACC64 the diagonal components are
- * compensated float pairs, the six others and G float sums.  The handle's
- * scatter mode does not apply.  Requires mu > 0 (tau1 of an element at rest
+ * One warp per row (or per two rows of at most 16 entries): each element of
+ * the row's star is evaluated once, its contributions summed per entry in
+ * element order (deterministic); rows of more than 32 entries
+ * (NsiInfo.long_rows) and, in the mixed modes, the rows touching badly shaped
+ * elements (NsiInfo.exact_rows) are then computed by one double-precision
+ * thread per row.  Precision as nsi_assemble; in NSI_MIXED_F32_ACC64 the
+ * diagonal components are compensated float pairs, the six others and G
+ * float sums.  The handle's scatter mode does not apply.  NSI_ERR_UNSUPPORTED
+ * for meshes of more than 2^31 node-element incidences.  Requires mu > 0 (tau1 of an element at rest
  * is h^2 / (4 mu)), rho >= 0, dt > 0 (NSI_ERR_INVALID_ARG otherwise).
  * Never allocates or synchronises.
  */

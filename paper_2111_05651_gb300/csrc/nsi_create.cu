@@ -76,7 +76,8 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->exact_ptr);
   cudaFree(h->exact_inc);
   cudaFree(h->star_ptr);
-  cudaFree(h->star_inc);
+  cudaFree(h->star_word);
+  cudaFree(h->star_task);
   cudaFree(h->fan);
   cudaFree(h->fan_blk);
   cudaFree(h->xyz64);
@@ -748,15 +749,22 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->exact_ptr, exact_ptr.data(), exact_ptr.size(), s))) return st;
     if ((st = dev_upload(h, &h->exact_inc, exact_inc.data(), exact_inc.size(), s))) return st;
   }
-  // the stabilised block's per-row kernel needs every row's elements when
-  // there is no fan map (host copies kept until the uploads have completed)
-  std::vector<int32_t> star_ptr_h;
-  std::vector<uint32_t> star_inc_h;
-  if (!h->fan_ok && E <= (int64_t)(UINT32_MAX >> 2) && inc_ptr[n] <= INT32_MAX) {
+  // the stabilised block's row kernel: star offsets and words, and warp
+  // tasks of one row (up to 32 entries, or a long row, which the kernel
+  // skips) or two consecutive rows of at most 16 entries each
+  std::vector<int32_t> star_ptr_h, star_task;
+  if (h->gather_ok) {
     star_ptr_h.assign(inc_ptr.begin(), inc_ptr.end());
-    star_inc_h.assign(inc.begin(), inc.end());
+    for (int64_t i = 0; i < n;) {
+      star_task.push_back((int32_t)i);
+      const bool pair = i + 1 < n && !is_long[i] && !is_long[i + 1] && row_len[i] <= 16 && row_len[i + 1] <= 16;
+      i += pair ? 2 : 1;
+    }
+    star_task.push_back((int32_t)n);
+    h->n_star_tasks = (int64_t)star_task.size() - 1;
     if ((st = dev_upload(h, &h->star_ptr, star_ptr_h.data(), star_ptr_h.size(), s))) return st;
-    if ((st = dev_upload(h, &h->star_inc, star_inc_h.data(), star_inc_h.size(), s))) return st;
+    if ((st = dev_upload(h, &h->star_word, star.data(), star.size(), s))) return st;
+    if ((st = dev_upload(h, &h->star_task, star_task.data(), star_task.size(), s))) return st;
   }
   if (h->precision == NSI_FP64) {
     if ((st = dev_upload(h, &h->xyz64, xyz64.data(), n, s))) return st;

@@ -191,10 +191,14 @@ struct NsiHandle {
   int32_t* exact_list = nullptr;  // [exact_rows] their node ids
   int32_t* exact_ptr = nullptr;   // [exact_rows + 1] into exact_inc
   uint32_t* exact_inc = nullptr;  // element * 4 + local index of the row's node
-  // meshes without an edge-fan map: every row's incident elements, for the
-  // stabilised block's per-row kernel (null when the fan map exists)
-  int32_t* star_ptr = nullptr;   // [n + 1] into star_inc
-  uint32_t* star_inc = nullptr;  // element * 4 + local index of the row's node
+  // the stabilised block's row kernel: every row's star as row positions of
+  // each element's other three nodes (five bits each, the row's node and the
+  // three in a positively oriented order), and its warp tasks (one row, or two
+  // consecutive rows of at most 16 entries); long rows are left out
+  int32_t* star_ptr = nullptr;    // [n + 1] into star_word
+  uint16_t* star_word = nullptr;  // [incidences]
+  int32_t* star_task = nullptr;   // [n_star_tasks + 1] first row of every task
+  int64_t n_star_tasks = 0;
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory
   int n_plans = 0;

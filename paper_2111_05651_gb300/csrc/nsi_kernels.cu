@@ -2146,146 +2146,253 @@ __device__ __forceinline__ T stab_terms(const V3<T>& ci, const V3<T>& cj, T det,
   return k.ks * mm * rcp_fast(h * fma_of(k.krh, sh, k.k4mu));
 }
 
-// shared memory of a stabilised fan block (T entries): the records, the row
-// starts, the A + S and lumped-mass accumulators, and twelve arrays of plain
-// sums (K's nine components, then G's three)
+// Shared memory of one warp of the stabilised row kernel (component-major,
+// 32 lanes): entry records (edge vector from the row's node, velocity),
+// element records (the cofactors c1, c2, c3 of the element's other three
+// nodes, c_i, mu/(6 det), tau2/(6 det), det, and the three A + S
+// contributions), the elements' star words, and one bit mask of elements per
+// entry.
 template <int P>
-struct StabFanSmem {
+struct StarSmem {
   using T = typename Prec<P>::T;
-  static constexpr size_t rp(int Tn) { return 2 * sizeof(T4<T>) * (size_t)Tn; }
-  static constexpr size_t red(int Tn) { return rp(Tn) + (((size_t)4 * (Tn + 1) + 15) & ~size_t(15)); }
-  static constexpr size_t vals(int Tn) { return red(Tn) + 2 * sizeof(Acc<P>) * (size_t)Tn; }
-  static constexpr size_t total(int Tn) { return vals(Tn) + 12 * sizeof(T) * (size_t)Tn; }
+  static constexpr int NE = 6, NL = 18;
+  static constexpr size_t ent() { return 0; }
+  static constexpr size_t el() { return sizeof(T) * NE * 32; }
+  static constexpr size_t pos() { return el() + sizeof(T) * NL * 32; }
+  static constexpr size_t mask() { return pos() + 2 * 32; }
+  static constexpr size_t bytes() { return mask() + 4 * 32; }
 };
+constexpr int STAR_WARPS = 4;  // warps (tasks) per block
 
-// The stabilised block by edge fans: one thread per CSR entry (i, j) of a
-// block of whole rows, as fan_block.  An off-diagonal entry sums over the
-// elements (i, j, k_m, k_m+1) around its edge, in registers: A + S (one
-// accumulator, compensated in mixed64), K's nine components and G's three
-// (plain sums of at most seven elements), det for the lumped mass.  The row
-// totals reach the diagonal through a tree reduction in shared memory.  Every
-// output is written once, coalesced across the block: Auu component-major,
-// then G and the right-hand side as the Galerkin assembly.
+// The stabilised block by rows, one warp per task (one row of up to 32
+// entries, or two consecutive rows of up to 16 on the two half-warps).
+//  1. Each entry lane loads its column's node record; the edge vector from the
+//     row's node (the diagonal lane's record, by shuffles) and the velocity go
+//     to shared memory.
+//  2. In passes of 32, each lane takes one element of the task's stars (node
+//     i first, the others in a positively oriented order, from the star
+//     word): cofactors, det, c_i, w = rho/120 (2 u_i + u_1 + u_2 + u_3) +
+//     mu/(6 det) c_i, Codina's tau from h = det^(1/3) and the velocity sum,
+//     the SUPG vector v = fs [(us . c_i) us + sum_n (u_n . c_i) u_n], and the
+//     contributions (w + v) . c_k to its three entries; its record goes to
+//     shared memory and its bit into the masks of those three entries.
+//  3. Each off-diagonal entry lane adds, in element order, the records of its
+//     masked elements: A + S, K += kv c_k x c_i + kd c_i x c_k, G's c_i sum and
+//     det for the lumped mass.
+//  4. A butterfly over the row's lanes gives the row totals; the diagonal
+//     block is the lumped mass times I minus the off-diagonal blocks' sum.
+//  5. Every lane writes its own entry (the row's slice of each output array
+//     is contiguous); the diagonal lane writes the right-hand side.
+// Each element is evaluated once per row of its star (four times per tet).
+// Long rows (more than 32 entries, or a star the row-gather encoder could
+// not cover) are single-row tasks this kernel skips.
 template <int P, bool DEBUG>
-__global__ void __launch_bounds__(FAN_BLOCK) stab_fan_kernel(MeshView m, FieldView f, StabConst sc, void* Auu,
-                                                             void* Gv, void* rhs) {
+__global__ void __launch_bounds__(32 * STAR_WARPS) stab_star_kernel(MeshView m, FieldView f, StabConst sc,
+                                                                    const int32_t* __restrict__ tasks, int64_t ntasks,
+                                                                    const int32_t* __restrict__ star_ptr,
+                                                                    const uint16_t* __restrict__ star_word,
+                                                                    void* Auu, void* Gv, void* rhs) {
   extern __shared__ __align__(16) unsigned char smem[];
   using T = typename Prec<P>::T;
   using Out = typename Prec<P>::Out;
-  constexpr int TB = FAN_BLOCK;
-  T4<T>* rec0 = reinterpret_cast<T4<T>*>(smem);
-  T4<T>* rec1 = rec0 + TB;
-  int32_t* rp = reinterpret_cast<int32_t*>(smem + StabFanSmem<P>::rp(TB));
-  Acc<P>* rA = reinterpret_cast<Acc<P>*>(smem + StabFanSmem<P>::red(TB));
-  Acc<P>* rD = rA + TB;
-  T* rv = reinterpret_cast<T*>(smem + StabFanSmem<P>::vals(TB));
-  const int k = threadIdx.x;
-  FanEntry<T> fe;
-  if (!fan_entry<P, DEBUG>(m, blockIdx.x, rec0, rec1, rp, fe)) return;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t task = (int64_t)blockIdx.x * STAR_WARPS + (threadIdx.x >> 5);
+  if (task >= ntasks) return;  // warp-uniform
+  unsigned char* ws = smem + (threadIdx.x >> 5) * StarSmem<P>::bytes();
+  T* er = reinterpret_cast<T*>(ws + StarSmem<P>::ent());
+  T* el = reinterpret_cast<T*>(ws + StarSmem<P>::el());
+  uint16_t* ew = reinterpret_cast<uint16_t*>(ws + StarSmem<P>::pos());
+  unsigned* mk = reinterpret_cast<unsigned*>(ws + StarSmem<P>::mask());
+
+  const int32_t r0 = tasks[task];
+  const int nrow = tasks[task + 1] - r0;  // 1 or 2
+  const int width = nrow == 2 ? 16 : 32;
+  const int seg = nrow == 2 ? lane >> 4 : 0;
+  const int q = lane - seg * width;  // this lane's position in its row
+  const int64_t i = r0 + seg;
+  const int32_t rs = m.row_ptr[i], len = m.row_ptr[i + 1] - rs;
+  const int dp = m.diag_pos[i];
+  if (nrow == 1 && (len > 32 || dp == DIAG_LONG)) return;  // a long row: the per-row kernel's
+  if (DEBUG && (len > width || (len > 0 && dp >= len))) {
+    atomicOr(m.err, ERR_STAR);
+    return;
+  }
+  const bool has = q < len;
   const T kc = kc_of<T>(f), kmu = kmu_of<T>(f), kmass = kmass_of<T>(f);
   const StabK<T> sk = stab_k<T>(sc);
   const T kg = (T)(-1.0 / 24.0);
 
+  // 1. entry records
+  {
+    const int j = has ? m.col_idx[rs + q] : 0;
+    if (DEBUG && has && (j < 0 || j >= m.n)) atomicOr(m.err, ERR_BAD_INDEX);
+    const int dl = seg * width + (len > 0 ? dp : 0);  // the diagonal's lane
+    V3<T> d, u;
+    if constexpr (P == NSI_FP64) {
+      D4 x{0.0, 0.0, 0.0, 0.0}, v{0.0, 0.0, 0.0, 0.0};
+      if (has && (!DEBUG || (j >= 0 && j < m.n))) {
+        const D4* r = static_cast<const D4*>(m.rec) + 2 * (int64_t)j;
+        x = r[0];
+        v = r[1];
+      }
+      const double xi = __shfl_sync(FULL, x.x, dl), yi = __shfl_sync(FULL, x.y, dl), zi = __shfl_sync(FULL, x.z, dl);
+      d = {x.x - xi, x.y - yi, x.z - zi};
+      u = {v.x, v.y, v.z};
+    } else {
+      uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+      if (has && (!DEBUG || (j >= 0 && j < m.n))) {
+        const uint4* r = static_cast<const uint4*>(m.rec) + 2 * (int64_t)j;
+        a = __ldg(r);
+        b = __ldg(r + 1);
+      }
+      const V3<float> hj{__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+      const V3<float> lj = record_lo(__uint_as_float(b.z), __uint_as_float(b.w));
+      const V3<float> hi{__shfl_sync(FULL, hj.x, dl), __shfl_sync(FULL, hj.y, dl), __shfl_sync(FULL, hj.z, dl)};
+      const V3<float> li{__shfl_sync(FULL, lj.x, dl), __shfl_sync(FULL, lj.y, dl), __shfl_sync(FULL, lj.z, dl)};
+      d = add(sub(hj, hi), sub(lj, li));
+      u = {__uint_as_float(a.w), __uint_as_float(b.x), __uint_as_float(b.y)};
+    }
+    er[0 * 32 + lane] = d.x;
+    er[1 * 32 + lane] = d.y;
+    er[2 * 32 + lane] = d.z;
+    er[3 * 32 + lane] = u.x;
+    er[4 * 32 + lane] = u.y;
+    er[5 * 32 + lane] = u.z;
+  }
+  __syncwarp();
+
+  // 2-3. elements in passes of 32, then the entries' sums
+  const int dp0 = __shfl_sync(FULL, dp, 0), dp1 = __shfl_sync(FULL, dp, 16);
+  const int len0 = __shfl_sync(FULL, len, 0), len1 = __shfl_sync(FULL, len, 16);
+  const int64_t s0 = star_ptr[r0], s1 = star_ptr[r0 + 1], s2 = nrow == 2 ? star_ptr[r0 + 2] : s1;
+  const int nel = (int)(s2 - s0);
   Acc<P> sA, sD;
   sA.zero();
   sD.zero();
-  T sK[9], sG[3] = {T(0), T(0), T(0)};
+  T K[9], G[3] = {T(0), T(0), T(0)};
 #pragma unroll
-  for (int c = 0; c < 9; ++c) sK[c] = T(0);
-  const int nring = (fe.w >> 24) & 7;
-  if (k < fe.L && nring > 0) {
-    const bool closed = (fe.w >> 27) & 1;
-    const int nel = closed ? nring : nring - 1;
-    const V3<T> dj = fe.dj, uj = fe.uj, ui = fe.ui;
-    const V3<T> uij{ui.x + ui.x + uj.x, ui.y + ui.y + uj.y, ui.z + ui.z + uj.z};  // 2 u_i + u_j
-    auto node = [&](int mpos, V3<T>& d, V3<T>& u) {
-      const int pos = (fe.w >> (4 * mpos)) & 15;
-      if (DEBUG && pos >= fe.len) atomicOr(m.err, ERR_STAR);
-      const T4<T> x = rec0[fe.a + pos], y = rec1[fe.a + pos];
-      d = {x.x, x.y, x.z};
-      u = {y.x, y.y, y.z};
-    };
-    V3<T> d0, u0;
-    node(0, d0, u0);
-    V3<T> q0 = cross(dj, d0);
-    const V3<T> dfirst = d0, ufirst = u0, qfirst = q0;
-    for (int e = 0; e < nel; ++e) {
-      V3<T> d1, u1, q1;
-      if (e + 1 < nring) {
-        node(e + 1, d1, u1);
-        q1 = cross(dj, d1);
-      } else {  // closing element of an interior ring
-        d1 = dfirst;
-        u1 = ufirst;
-        q1 = qfirst;
+  for (int c = 0; c < 9; ++c) K[c] = T(0);
+  for (int p0 = 0; p0 < nel; p0 += 32) {
+    mk[lane] = 0u;
+    __syncwarp();
+    const int t = p0 + lane;
+    if (t < nel) {
+      const int es = (nrow == 2 && s0 + t >= s1) ? 1 : 0;  // the element's row
+      const int eb = es * width;
+      const int edp = es ? dp1 : dp0;
+      const unsigned w = star_word[s0 + t];
+      const int pa = w & 31, pb = (w >> 5) & 31, pc = (w >> 10) & 31;
+      if (DEBUG && (pa >= (es ? len1 : len0) || pb >= (es ? len1 : len0) || pc >= (es ? len1 : len0)))
+        atomicOr(m.err, ERR_STAR);
+      auto rd = [&](int l, int c0) { return V3<T>{er[c0 * 32 + l], er[(c0 + 1) * 32 + l], er[(c0 + 2) * 32 + l]}; };
+      const V3<T> d1 = rd(eb + pa, 0), d2 = rd(eb + pb, 0), d3 = rd(eb + pc, 0);
+      const V3<T> u1 = rd(eb + pa, 3), u2 = rd(eb + pb, 3), u3 = rd(eb + pc, 3), ui = rd(eb + edp, 3);
+      const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
+      const T det = dot(d1, c1);
+      const V3<T> ci{-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
+      const T rdet = rcp_fast(det);
+      const T kv = kmu * rdet;
+      const V3<T> us = add(add(ui, u1), add(u2, u3));
+      const T h = cbrt_of(det);
+      const T sh = sqrt_of(dot(us, us)) * h;
+      const T fs = sk.ks * rcp_fast(h * fma_of(sk.krh, sh, sk.k4mu));
+      const T kd = fma_of(sk.kr48 * sh, rdet, kv);
+      const T as = dot(us, ci), ai = dot(ui, ci), a1 = dot(u1, ci), a2 = dot(u2, ci), a3 = dot(u3, ci);
+      // w + v: Galerkin convection and viscosity plus the SUPG vector
+      V3<T> wv;
+      wv.x = kc * (ui.x + us.x) + kv * ci.x + fs * (as * us.x + ai * ui.x + a1 * u1.x + a2 * u2.x + a3 * u3.x);
+      wv.y = kc * (ui.y + us.y) + kv * ci.y + fs * (as * us.y + ai * ui.y + a1 * u1.y + a2 * u2.y + a3 * u3.y);
+      wv.z = kc * (ui.z + us.z) + kv * ci.z + fs * (as * us.z + ai * ui.z + a1 * u1.z + a2 * u2.z + a3 * u3.z);
+      const T vals[18] = {c1.x, c1.y, c1.z, c2.x, c2.y, c2.z, c3.x, c3.y, c3.z, ci.x, ci.y, ci.z,
+                          kv, kd, det, dot(wv, c1), dot(wv, c2), dot(wv, c3)};
+#pragma unroll
+      for (int c = 0; c < 18; ++c) el[c * 32 + lane] = vals[c];
+      ew[lane] = (uint16_t)w;
+      atomicOr(&mk[eb + pa], 1u << lane);
+      atomicOr(&mk[eb + pb], 1u << lane);
+      atomicOr(&mk[eb + pc], 1u << lane);
+    }
+    __syncwarp();
+    if (has && q != dp) {
+      unsigned bits = mk[lane];
+      while (bits) {
+        const int e = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const unsigned w = ew[e];
+        const int k = (int)(w & 31) == q ? 0 : (int)((w >> 5) & 31) == q ? 1 : 2;
+        const V3<T> ck{el[(3 * k) * 32 + e], el[(3 * k + 1) * 32 + e], el[(3 * k + 2) * 32 + e]};
+        const T cix = el[9 * 32 + e], ciy = el[10 * 32 + e], ciz = el[11 * 32 + e];
+        const T kv = el[12 * 32 + e], kd = el[13 * 32 + e];
+        sA.add(el[(15 + k) * 32 + e]);
+        sD.add(el[14 * 32 + e]);
+        const T r[3] = {cix, ciy, ciz}, c[3] = {ck.x, ck.y, ck.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2)
+            K[3 * a + b2] = fma_of(kv * c[a], r[b2], fma_of(kd * r[a], c[b2], K[3 * a + b2]));
+        G[0] += cix;
+        G[1] += ciy;
+        G[2] += ciz;
       }
-      const V3<T> cj = cross(d0, d1);
-      const T det = dot(dj, cj);
-      const V3<T> ci{-(cj.x + q0.x - q1.x), -(cj.y + q0.y - q1.y), -(cj.z + q0.z - q1.z)};
-      const T kv = kmu * rcp_fast(det);
-      const V3<T> w3{kc * (uij.x + u0.x + u1.x) + kv * ci.x, kc * (uij.y + u0.y + u1.y) + kv * ci.y,
-                     kc * (uij.z + u0.z + u1.z) + kv * ci.z};
-      const T st = stab_terms<T>(ci, cj, det, ui, uj, u0, u1, sk, kmu, sK);
-      sA.add(dot(w3, cj) + st);
-      sG[0] += ci.x;
-      sG[1] += ci.y;
-      sG[2] += ci.z;
-      sD.add(det);
-      d0 = d1;
-      u0 = u1;
-      q0 = q1;
     }
+    __syncwarp();
   }
 
-  // row totals for the diagonal block
-  if (k < fe.L) {
-    rA[k] = sA;
-    rD[k] = sD;
+  // 4. row totals (lanes without an off-diagonal entry hold zeros)
+  Acc<P> tA = sA, tD = sD;
+  T tK[9], tG[3];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) rv[c * TB + k] = sK[c];
+  for (int c = 0; c < 9; ++c) tK[c] = K[c];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) rv[(9 + d) * TB + k] = sG[d];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int st = 1; st < FAN_MAX_ROW; st <<= 1) {
-    if (k < fe.L && ((k - fe.a) & (2 * st - 1)) == 0 && k - fe.a + st < fe.len) {
-      acc_merge<P>(rA[k], rA[k + st]);
-      acc_merge<P>(rD[k], rD[k + st]);
-#pragma unroll
-      for (int c = 0; c < 12; ++c) rv[c * TB + k] += rv[c * TB + k + st];
+  for (int c = 0; c < 3; ++c) tG[c] = G[c];
+  for (int o = 1; o < width; o <<= 1) {
+    Acc<P> xA, xD;
+    if constexpr (P == NSI_MIXED_F32_ACC64) {
+      xA.hi = __shfl_xor_sync(FULL, tA.hi, o);
+      xA.lo = __shfl_xor_sync(FULL, tA.lo, o);
+      xD.hi = __shfl_xor_sync(FULL, tD.hi, o);
+      xD.lo = __shfl_xor_sync(FULL, tD.lo, o);
+    } else {
+      xA.v = __shfl_xor_sync(FULL, tA.v, o);
+      xD.v = __shfl_xor_sync(FULL, tD.v, o);
     }
-    __syncthreads();
+    acc_merge<P>(tA, xA);
+    acc_merge<P>(tD, xD);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tK[c] += __shfl_xor_sync(FULL, tK[c], o);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tG[c] += __shfl_xor_sync(FULL, tG[c], o);
   }
 
+  // 5. write-out
   Out* A = static_cast<Out*>(Auu);
-  Out* G = static_cast<Out*>(Gv);
+  Out* Go = static_cast<Out*>(Gv);
   Out* Rh = static_cast<Out*>(rhs);
-  if (k < fe.L) {
-    const int64_t g = (int64_t)fe.base + k;
-    if (k == fe.a + fe.dp) {
-      const Acc<P> mass = acc_scale<P>(acc_third<P>(rD[fe.a]), kmass);
+  if (has) {
+    const int64_t g = (int64_t)rs + q;
+    if (q == dp) {
+      const Acc<P> mass = acc_scale<P>(acc_third<P>(tD), kmass);
       Acc<P> dA = mass;
       if constexpr (P == NSI_MIXED_F32_ACC64) {
-        dA.add(-rA[fe.a].hi);
-        dA.lo -= rA[fe.a].lo;
+        dA.add(-tA.hi);
+        dA.lo -= tA.lo;
       } else {
-        dA.v = mass.v - rA[fe.a].v;
+        dA.v = mass.v - tA.v;
       }
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const T kt = -rv[c * TB + fe.a];
         if (c % 4 == 0) {
-          Acc<P> t = dA;
-          t.add(kt);
-          store_acc(A + c * m.nnz + g, t);
+          Acc<P> x = dA;
+          x.add(-tK[c]);
+          store_acc(A + c * m.nnz + g, x);
         } else {
-          A[c * m.nnz + g] = (Out)kt;
+          A[c * m.nnz + g] = (Out)(-tK[c]);
         }
       }
 #pragma unroll
-      for (int d = 0; d < 3; ++d) G[d * m.nnz + g] = (Out)(rv[(9 + d) * TB + fe.a] * (kg / T(3)));
-      const int64_t i = fe.R0 + fe.row;
+      for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(tG[c] * (kg / T(3)));
       const V3<T> un = load_vec<T>(f.un, i);
       store_acc(Rh + i, acc_scale<P>(mass, un.x));
       store_acc(Rh + m.n + i, acc_scale<P>(mass, un.y));
@@ -2294,24 +2401,20 @@ __global__ void __launch_bounds__(FAN_BLOCK) stab_fan_kernel(MeshView m, FieldVi
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         if (c % 4 == 0) {
-          Acc<P> t = sA;
-          t.add(sK[c]);
-          store_acc(A + c * m.nnz + g, t);
+          Acc<P> x = sA;
+          x.add(K[c]);
+          store_acc(A + c * m.nnz + g, x);
         } else {
-          A[c * m.nnz + g] = (Out)sK[c];
+          A[c * m.nnz + g] = (Out)K[c];
         }
       }
 #pragma unroll
-      for (int d = 0; d < 3; ++d) G[d * m.nnz + g] = (Out)(sG[d] * kg);
+      for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(G[c] * kg);
     }
-  }
-  // rows without entries (nodes in no element): zero right-hand side
-  for (int r = k; r < fe.nr; r += TB) {
-    if (rp[r + 1] == rp[r]) {
-      Rh[fe.R0 + r] = Out(0);
-      Rh[m.n + fe.R0 + r] = Out(0);
-      Rh[2 * m.n + fe.R0 + r] = Out(0);
-    }
+  } else if (q == 0 && len == 0) {  // a node in no element: zero right-hand side
+    Rh[i] = Out(0);
+    Rh[m.n + i] = Out(0);
+    Rh[2 * m.n + i] = Out(0);
   }
 }
 
@@ -3338,33 +3441,38 @@ static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOut
   return NSI_OK;
 }
 
-// the stabilised velocity block: pack and the fan kernel (then, in the mixed
-// modes, the rows touching badly shaped elements in double), or the per-row
-// kernel over every row when the mesh has no fan map
-static_assert(StabFanSmem<NSI_FP64>::total(FAN_BLOCK) <= 48 * 1024, "stabilised fan block above 48 KB");
+// the stabilised velocity block: pack, the row kernel over every task, then
+// the long rows and (mixed modes) the rows touching badly shaped elements by
+// the per-row double kernel
 template <int P>
 static nsi_status stabilized_p(NsiHandle* h, const FieldView& f, const StabConst& sc, void* Auu, void* G, void* rhs,
                                cudaStream_t s) {
   if (h->n == 0) return NSI_OK;
+  if (!h->gather_ok || !h->star_task)
+    return fail(NSI_ERR_UNSUPPORTED, "the stabilised block needs the row maps (more than 2^31 node-element incidences)");
   MeshView m = view_of(h);
-  if (h->fan_ok) {
-    const size_t smem = StabFanSmem<P>::total(FAN_BLOCK);
-    pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
-    if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
-    if (h->debug) stab_fan_kernel<P, true><<<h->fan_blocks, FAN_BLOCK, smem, s>>>(m, f, sc, Auu, G, rhs);
-    else stab_fan_kernel<P, false><<<h->fan_blocks, FAN_BLOCK, smem, s>>>(m, f, sc, Auu, G, rhs);
-    if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
-    nsi_status st = check_launch("stab_fan_kernel");
-    if (st || P == NSI_FP64 || h->exact_rows == 0) return st;
-    stab_rows_kernel<P><<<(h->exact_rows + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, h->exact_list, h->exact_ptr,
-                                                                  h->exact_inc, h->exact_rows);
-    return check_launch("stab_rows_kernel (exact rows)");
-  }
-  if (!h->star_ptr) return fail(NSI_ERR_UNSUPPORTED, "no row incidence for the stabilised block of this mesh");
+  pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
+  const size_t smem = StarSmem<P>::bytes() * STAR_WARPS;
+  const int64_t grid = (h->n_star_tasks + STAR_WARPS - 1) / STAR_WARPS;
   if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
-  stab_rows_kernel<P><<<(h->n + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, nullptr, h->star_ptr, h->star_inc, h->n);
+  if (h->debug)
+    stab_star_kernel<P, true><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks, h->star_ptr,
+                                                                   h->star_word, Auu, G, rhs);
+  else
+    stab_star_kernel<P, false><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks,
+                                                                    h->star_ptr, h->star_word, Auu, G, rhs);
   if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
-  return check_launch("stab_rows_kernel");
+  nsi_status st = check_launch("stab_star_kernel");
+  if (st) return st;
+  if (h->long_rows > 0) {
+    stab_rows_kernel<P><<<(h->long_rows + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, h->long_list, h->long_ptr,
+                                                                 h->long_inc, h->long_rows);
+    if ((st = check_launch("stab_rows_kernel (long rows)"))) return st;
+  }
+  if (P == NSI_FP64 || h->exact_rows == 0) return NSI_OK;
+  stab_rows_kernel<P><<<(h->exact_rows + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, h->exact_list, h->exact_ptr,
+                                                                h->exact_inc, h->exact_rows);
+  return check_launch("stab_rows_kernel (exact rows)");
 }
 
 extern "C" {

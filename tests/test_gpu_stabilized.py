@@ -6,10 +6,11 @@ viscous coupling and the grad-div term of Codina's algebraic subgrid scales),
 G and rhs against the FP64 oracle, row-scaled per component.  Bars as the
 Galerkin assembly: FP64 1e-12, mixed modes 1e-5 (against the oracle on the
 float velocities the kernels receive, and on the original double ones).
-Paths: the edge-fan kernel (Kuhn meshes), the per-row double kernel (a
-Delaunay mesh without a fan map), the fan kernel plus the double rows of
-badly shaped elements (a sliver mesh, mixed modes), and the 100^3 cube at
-full size on sampled rows.
+Paths: the row kernel (one warp per row or pair of rows; Kuhn meshes, a
+Delaunay mesh with rows of up to 32 entries), the per-row double kernel for
+rows of more than 32 entries (a hub mesh) and, in the mixed modes, for the
+rows of badly shaped elements (a sliver mesh), and the 100^3 cube at full
+size on sampled rows.
 """
 import numpy as np
 import pytest
@@ -75,11 +76,11 @@ CASES = [
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
-def test_stabilized_fan_parity(case, precision):
+def test_stabilized_parity(case, precision):
     name, kw = case
     mesh, u = meshgen.config_mesh(kw["name"]) if "name" in kw else meshgen.config_mesh(**kw)
     info = check(mesh, u, precision)
-    assert info.fan_ok == 1
+    assert info.long_rows == 0 and info.max_row <= 16
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
@@ -98,25 +99,35 @@ def test_stabilized_separate_rhs_velocity(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
-def test_stabilized_without_fan_map(precision):
-    """A Delaunay mesh (irregular stars, rings of more than 7 elements): no fan
-    map, so every row runs the per-row double kernel."""
+def test_stabilized_unstructured_mesh(precision):
+    """A Delaunay mesh: irregular stars, rows of 17..32 entries on whole-warp
+    tasks, slivers."""
     mesh, u = meshgen.delaunay_cube(8, 0.25, seed=7)
     info = check(mesh, u, precision)
-    assert info.fan_ok == 0
+    assert info.max_row > 16 and info.long_rows == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_stabilized_long_rows(precision):
+    """A hub node joined to 48 surrounding nodes: its row (and its
+    neighbours' longer rows) exceed 32 entries and go to the per-row double
+    kernel; the rest of the mesh stays on the row kernel."""
+    mesh, u = meshgen.delaunay_hub()
+    info = check(mesh, u, precision)
+    assert info.long_rows > 0
 
 
 @pytest.mark.parametrize("precision", ["mixed64", "mixed32"])
 def test_stabilized_badly_shaped_elements(precision):
     """4^3 Kuhn cube with node (2,2,2) moved by 0.499 h along (1,-1,0): two
     slivers (|d1||d2||d3| / det about 1.1e3); their rows are recomputed in
-    double after the fan kernel."""
+    double after the row kernel."""
     mesh, u = meshgen.config_mesh(N=4, jitter=0.0, numbering="natural", seed=0)
     coord = mesh.coord.copy()
     coord[2 + 5 * (2 + 5 * 2)] += 0.499 * 0.25 * np.array([1.0, -1.0, 0.0])
     mesh = meshgen.Mesh(coord=coord, lnods=mesh.lnods, N=4)
     info = check(mesh, u, precision)
-    assert info.fan_ok == 1 and info.exact_rows > 0
+    assert info.exact_rows > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed64"])
@@ -162,7 +173,6 @@ def test_stabilized_cube100_sampled_rows(cube100, precision):
     stabilised assembly, pattern of those rows bit-exact."""
     mesh, u = cube100
     asm = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
-    assert asm.info().fan_ok == 1
     Auu, G, rhs = asm.assemble_stabilized(torch.as_tensor(u.T.copy()), rho=RHO, mu=MU, dt=DT)
     torch.cuda.synchronize()
     rp, ci = (t.cpu().numpy() for t in asm.pattern())
