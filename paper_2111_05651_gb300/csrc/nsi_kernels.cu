@@ -2146,21 +2146,34 @@ __device__ __forceinline__ T stab_terms(const V3<T>& ci, const V3<T>& cj, T det,
   return k.ks * mm * rcp_fast(h * fma_of(k.krh, sh, k.k4mu));
 }
 
-// Shared memory of one warp of the stabilised row kernel (component-major,
-// 32 lanes): entry records (edge vector from the row's node, velocity),
-// element records (the cofactors c1, c2, c3 of the element's other three
-// nodes, c_i, mu/(6 det), tau2/(6 det), det, and the three A + S
-// contributions), the elements' star words, and one bit mask of elements per
-// entry.
+// Lengths of Codina's tau for one element: h = det^(1/3) and s h with s the
+// norm of the four velocities' sum.  Float: h from the exp2/log2 estimate and
+// one Newton step for the cube root (h <- (2 h + det / h^2) / 3), s as
+// s2 rsqrt(s2) (0 for s2 = 0); double: cbrt and sqrt.
+__device__ __forceinline__ void tau_lengths(float det, float s2, float& h, float& sh) {
+  const float h0 = exp2f(__log2f(det) * (1.0f / 3.0f));
+  h = fmaf(h0, 2.0f / 3.0f, det * __fdividef(1.0f / 3.0f, h0 * h0));
+  sh = (s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f) * h;
+}
+__device__ __forceinline__ void tau_lengths(double det, double s2, double& h, double& sh) {
+  h = cbrt(det);
+  sh = sqrt(s2) * h;
+}
+
+// Shared memory of one warp of the stabilised row kernel: entry records
+// (component-major [6][32]: edge vector from the row's node, velocity), then
+// element records for a chunk of 64 elements (element-major, five T4 each:
+// (c_i, mu/(6 det)), (c_1, A+S to node 1), (c_2, ..), (c_3, ..),
+// (tau2/(6 det), det, -, -)), then per entry three 64-bit masks of the
+// chunk's elements holding the entry as their first, second or third node.
 template <int P>
 struct StarSmem {
   using T = typename Prec<P>::T;
-  static constexpr int NE = 6, NL = 18;
+  static constexpr int CHUNK = 64;
   static constexpr size_t ent() { return 0; }
-  static constexpr size_t el() { return sizeof(T) * NE * 32; }
-  static constexpr size_t pos() { return el() + sizeof(T) * NL * 32; }
-  static constexpr size_t mask() { return pos() + 2 * 32; }
-  static constexpr size_t bytes() { return mask() + 4 * 32; }
+  static constexpr size_t el() { return sizeof(T) * 6 * 32; }
+  static constexpr size_t mask() { return el() + sizeof(T4<T>) * 5 * CHUNK; }
+  static constexpr size_t bytes() { return mask() + sizeof(unsigned) * 6 * 32; }
 };
 constexpr int STAR_WARPS = 4;  // warps (tasks) per block
 
@@ -2169,13 +2182,13 @@ constexpr int STAR_WARPS = 4;  // warps (tasks) per block
 //  1. Each entry lane loads its column's node record; the edge vector from the
 //     row's node (the diagonal lane's record, by shuffles) and the velocity go
 //     to shared memory.
-//  2. In passes of 32, each lane takes one element of the task's stars (node
-//     i first, the others in a positively oriented order, from the star
-//     word): cofactors, det, c_i, w = rho/120 (2 u_i + u_1 + u_2 + u_3) +
-//     mu/(6 det) c_i, Codina's tau from h = det^(1/3) and the velocity sum,
-//     the SUPG vector v = fs [(us . c_i) us + sum_n (u_n . c_i) u_n], and the
-//     contributions (w + v) . c_k to its three entries; its record goes to
-//     shared memory and its bit into the masks of those three entries.
+//  2. In chunks of 64 elements (two per lane), each lane takes elements of the
+//     task's stars (node i first, the others in a positively oriented order,
+//     from the star word): cofactors, det, c_i, w = rho/120 (2 u_i + u_1 +
+//     u_2 + u_3) + mu/(6 det) c_i, Codina's tau from h = det^(1/3) and the
+//     velocity sum, the SUPG vector v = fs [(us . c_i) us + sum_n (u_n . c_i) u_n],
+//     and the contributions (w + v) . c_k to its three entries; its record
+//     goes to shared memory and its bit into those entries' masks.
 //  3. Each off-diagonal entry lane adds, in element order, the records of its
 //     masked elements: A + S, K += kv c_k x c_i + kd c_i x c_k, G's c_i sum and
 //     det for the lumped mass.
@@ -2196,17 +2209,24 @@ __global__ void __launch_bounds__(32 * STAR_WARPS) stab_star_kernel(MeshView m, 
   using T = typename Prec<P>::T;
   using Out = typename Prec<P>::Out;
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int CH = StarSmem<P>::CHUNK;
   const int lane = threadIdx.x & 31;
   const int64_t task = (int64_t)blockIdx.x * STAR_WARPS + (threadIdx.x >> 5);
   if (task >= ntasks) return;  // warp-uniform
   unsigned char* ws = smem + (threadIdx.x >> 5) * StarSmem<P>::bytes();
   T* er = reinterpret_cast<T*>(ws + StarSmem<P>::ent());
-  T* el = reinterpret_cast<T*>(ws + StarSmem<P>::el());
-  uint16_t* ew = reinterpret_cast<uint16_t*>(ws + StarSmem<P>::pos());
-  unsigned* mk = reinterpret_cast<unsigned*>(ws + StarSmem<P>::mask());
+  T4<T>* el = reinterpret_cast<T4<T>*>(ws + StarSmem<P>::el());
+  unsigned* mk = reinterpret_cast<unsigned*>(ws + StarSmem<P>::mask());  // [3 nodes][2 words][32 lanes]
 
   const int32_t r0 = tasks[task];
   const int nrow = tasks[task + 1] - r0;  // 1 or 2
+  // the stars' bounds and the first chunk's words, loaded ahead of the rows'
+  // records (independent of them)
+  const int64_t s0 = star_ptr[r0], s1 = star_ptr[r0 + 1], s2 = nrow == 2 ? star_ptr[r0 + 2] : s1;
+  const int nel = (int)(s2 - s0);
+  unsigned wpre[2];
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) wpre[hf] = hf * 32 + lane < nel ? star_word[s0 + hf * 32 + lane] : 0u;
   const int width = nrow == 2 ? 16 : 32;
   const int seg = nrow == 2 ? lane >> 4 : 0;
   const int q = lane - seg * width;  // this lane's position in its row
@@ -2262,79 +2282,86 @@ __global__ void __launch_bounds__(32 * STAR_WARPS) stab_star_kernel(MeshView m, 
   }
   __syncwarp();
 
-  // 2-3. elements in passes of 32, then the entries' sums
+  // 2-3. elements in chunks of 64, then the entries' sums
   const int dp0 = __shfl_sync(FULL, dp, 0), dp1 = __shfl_sync(FULL, dp, 16);
   const int len0 = __shfl_sync(FULL, len, 0), len1 = __shfl_sync(FULL, len, 16);
-  const int64_t s0 = star_ptr[r0], s1 = star_ptr[r0 + 1], s2 = nrow == 2 ? star_ptr[r0 + 2] : s1;
-  const int nel = (int)(s2 - s0);
   Acc<P> sA, sD;
   sA.zero();
   sD.zero();
   T K[9], G[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int c = 0; c < 9; ++c) K[c] = T(0);
-  for (int p0 = 0; p0 < nel; p0 += 32) {
-    mk[lane] = 0u;
-    __syncwarp();
-    const int t = p0 + lane;
-    if (t < nel) {
-      const int es = (nrow == 2 && s0 + t >= s1) ? 1 : 0;  // the element's row
-      const int eb = es * width;
-      const int edp = es ? dp1 : dp0;
-      const unsigned w = star_word[s0 + t];
-      const int pa = w & 31, pb = (w >> 5) & 31, pc = (w >> 10) & 31;
-      if (DEBUG && (pa >= (es ? len1 : len0) || pb >= (es ? len1 : len0) || pc >= (es ? len1 : len0)))
-        atomicOr(m.err, ERR_STAR);
-      auto rd = [&](int l, int c0) { return V3<T>{er[c0 * 32 + l], er[(c0 + 1) * 32 + l], er[(c0 + 2) * 32 + l]}; };
-      const V3<T> d1 = rd(eb + pa, 0), d2 = rd(eb + pb, 0), d3 = rd(eb + pc, 0);
-      const V3<T> u1 = rd(eb + pa, 3), u2 = rd(eb + pb, 3), u3 = rd(eb + pc, 3), ui = rd(eb + edp, 3);
-      const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
-      const T det = dot(d1, c1);
-      const V3<T> ci{-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
-      const T rdet = rcp_fast(det);
-      const T kv = kmu * rdet;
-      const V3<T> us = add(add(ui, u1), add(u2, u3));
-      const T h = cbrt_of(det);
-      const T sh = sqrt_of(dot(us, us)) * h;
-      const T fs = sk.ks * rcp_fast(h * fma_of(sk.krh, sh, sk.k4mu));
-      const T kd = fma_of(sk.kr48 * sh, rdet, kv);
-      const T as = dot(us, ci), ai = dot(ui, ci), a1 = dot(u1, ci), a2 = dot(u2, ci), a3 = dot(u3, ci);
-      // w + v: Galerkin convection and viscosity plus the SUPG vector
-      V3<T> wv;
-      wv.x = kc * (ui.x + us.x) + kv * ci.x + fs * (as * us.x + ai * ui.x + a1 * u1.x + a2 * u2.x + a3 * u3.x);
-      wv.y = kc * (ui.y + us.y) + kv * ci.y + fs * (as * us.y + ai * ui.y + a1 * u1.y + a2 * u2.y + a3 * u3.y);
-      wv.z = kc * (ui.z + us.z) + kv * ci.z + fs * (as * us.z + ai * ui.z + a1 * u1.z + a2 * u2.z + a3 * u3.z);
-      const T vals[18] = {c1.x, c1.y, c1.z, c2.x, c2.y, c2.z, c3.x, c3.y, c3.z, ci.x, ci.y, ci.z,
-                          kv, kd, det, dot(wv, c1), dot(wv, c2), dot(wv, c3)};
+  for (int c0 = 0; c0 < nel; c0 += CH) {
 #pragma unroll
-      for (int c = 0; c < 18; ++c) el[c * 32 + lane] = vals[c];
-      ew[lane] = (uint16_t)w;
-      atomicOr(&mk[eb + pa], 1u << lane);
-      atomicOr(&mk[eb + pb], 1u << lane);
-      atomicOr(&mk[eb + pc], 1u << lane);
+    for (int w = 0; w < 6; ++w) mk[w * 32 + lane] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int slot = half * 32 + lane;
+      const int t = c0 + slot;
+      if (t < nel) {
+        const int es = (nrow == 2 && s0 + t >= s1) ? 1 : 0;  // the element's row
+        const int eb = es * width;
+        const int edp = es ? dp1 : dp0;
+        const unsigned w = c0 == 0 ? wpre[half] : star_word[s0 + t];
+        const int pa = w & 31, pb = (w >> 5) & 31, pc = (w >> 10) & 31;
+        if (DEBUG && (pa >= (es ? len1 : len0) || pb >= (es ? len1 : len0) || pc >= (es ? len1 : len0)))
+          atomicOr(m.err, ERR_STAR);
+        auto rd = [&](int l, int c) { return V3<T>{er[c * 32 + l], er[(c + 1) * 32 + l], er[(c + 2) * 32 + l]}; };
+        const V3<T> d1 = rd(eb + pa, 0), d2 = rd(eb + pb, 0), d3 = rd(eb + pc, 0);
+        const V3<T> u1 = rd(eb + pa, 3), u2 = rd(eb + pb, 3), u3 = rd(eb + pc, 3), ui = rd(eb + edp, 3);
+        const V3<T> c1 = cross(d2, d3), c2 = cross(d3, d1), c3 = cross(d1, d2);
+        const T det = dot(d1, c1);
+        const V3<T> ci{-(c1.x + c2.x + c3.x), -(c1.y + c2.y + c3.y), -(c1.z + c2.z + c3.z)};
+        const T rdet = rcp_fast(det);
+        const T kv = kmu * rdet;
+        const V3<T> us = add(add(ui, u1), add(u2, u3));
+        T h, sh;
+        tau_lengths(det, dot(us, us), h, sh);
+        const T fs = sk.ks * rcp_fast(h * fma_of(sk.krh, sh, sk.k4mu));
+        const T kd = fma_of(sk.kr48 * sh, rdet, kv);
+        const T as = fs * dot(us, ci), ai = fs * dot(ui, ci), a1 = fs * dot(u1, ci), a2 = fs * dot(u2, ci),
+                a3 = fs * dot(u3, ci);
+        // w + v: Galerkin convection and viscosity plus the SUPG vector
+        V3<T> wv;
+        wv.x = kc * (ui.x + us.x) + kv * ci.x + (as * us.x + ai * ui.x + a1 * u1.x + a2 * u2.x + a3 * u3.x);
+        wv.y = kc * (ui.y + us.y) + kv * ci.y + (as * us.y + ai * ui.y + a1 * u1.y + a2 * u2.y + a3 * u3.y);
+        wv.z = kc * (ui.z + us.z) + kv * ci.z + (as * us.z + ai * ui.z + a1 * u1.z + a2 * u2.z + a3 * u3.z);
+        T4<T>* r = el + 5 * slot;
+        r[0] = T4<T>{ci.x, ci.y, ci.z, kv};
+        r[1] = T4<T>{c1.x, c1.y, c1.z, dot(wv, c1)};
+        r[2] = T4<T>{c2.x, c2.y, c2.z, dot(wv, c2)};
+        r[3] = T4<T>{c3.x, c3.y, c3.z, dot(wv, c3)};
+        r[4] = T4<T>{kd, det, T(0), T(0)};
+        const unsigned bit = 1u << lane;
+        atomicOr(&mk[(0 * 2 + half) * 32 + eb + pa], bit);
+        atomicOr(&mk[(1 * 2 + half) * 32 + eb + pb], bit);
+        atomicOr(&mk[(2 * 2 + half) * 32 + eb + pc], bit);
+      }
     }
     __syncwarp();
     if (has && q != dp) {
-      unsigned bits = mk[lane];
+      const unsigned long long m1 = mk[2 * 32 + lane] | ((unsigned long long)mk[3 * 32 + lane] << 32);
+      const unsigned long long m2 = mk[4 * 32 + lane] | ((unsigned long long)mk[5 * 32 + lane] << 32);
+      unsigned long long bits = mk[0 * 32 + lane] | ((unsigned long long)mk[1 * 32 + lane] << 32) | m1 | m2;
       while (bits) {
-        const int e = __ffs(bits) - 1;
+        const int e = __ffsll((long long)bits) - 1;
         bits &= bits - 1;
-        const unsigned w = ew[e];
-        const int k = (int)(w & 31) == q ? 0 : (int)((w >> 5) & 31) == q ? 1 : 2;
-        const V3<T> ck{el[(3 * k) * 32 + e], el[(3 * k + 1) * 32 + e], el[(3 * k + 2) * 32 + e]};
-        const T cix = el[9 * 32 + e], ciy = el[10 * 32 + e], ciz = el[11 * 32 + e];
-        const T kv = el[12 * 32 + e], kd = el[13 * 32 + e];
-        sA.add(el[(15 + k) * 32 + e]);
-        sD.add(el[14 * 32 + e]);
-        const T r[3] = {cix, ciy, ciz}, c[3] = {ck.x, ck.y, ck.z};
+        const int k = ((m1 >> e) & 1ull) ? 2 : ((m2 >> e) & 1ull) ? 3 : 1;
+        const T4<T>* r = el + 5 * e;
+        const T4<T> r0v = r[0], rk = r[k], r4 = r[4];
+        sA.add(rk.w);
+        sD.add(r4.y);
+        const T kv = r0v.w, kd = r4.x;
+        const T ri[3] = {r0v.x, r0v.y, r0v.z}, c[3] = {rk.x, rk.y, rk.z};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
           for (int b2 = 0; b2 < 3; ++b2)
-            K[3 * a + b2] = fma_of(kv * c[a], r[b2], fma_of(kd * r[a], c[b2], K[3 * a + b2]));
-        G[0] += cix;
-        G[1] += ciy;
-        G[2] += ciz;
+            K[3 * a + b2] = fma_of(kv * c[a], ri[b2], fma_of(kd * ri[a], c[b2], K[3 * a + b2]));
+        G[0] += ri[0];
+        G[1] += ri[1];
+        G[2] += ri[2];
       }
     }
     __syncwarp();
@@ -3441,6 +3468,18 @@ static nsi_status host_chunked_p(NsiHandle* h, const NsiFields* fd, const NsiOut
   return NSI_OK;
 }
 
+template <int P, bool DEBUG>
+static nsi_status set_star_smem() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(stab_star_kernel<P, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(StarSmem<P>::bytes() * STAR_WARPS));
+  });
+  if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute(stabilised row kernel smem)");
+  return NSI_OK;
+}
+
 // the stabilised velocity block: pack, the row kernel over every task, then
 // the long rows and (mixed modes) the rows touching badly shaped elements by
 // the per-row double kernel
@@ -3450,6 +3489,8 @@ static nsi_status stabilized_p(NsiHandle* h, const FieldView& f, const StabConst
   if (h->n == 0) return NSI_OK;
   if (!h->gather_ok || !h->star_task)
     return fail(NSI_ERR_UNSUPPORTED, "the stabilised block needs the row maps (more than 2^31 node-element incidences)");
+  nsi_status st = h->debug ? set_star_smem<P, true>() : set_star_smem<P, false>();
+  if (st) return st;
   MeshView m = view_of(h);
   pack_kernel<P><<<(h->n + 255) / 256, 256, 0, s>>>(m, f, const_cast<void*>(m.rec));
   const size_t smem = StarSmem<P>::bytes() * STAR_WARPS;
@@ -3462,7 +3503,7 @@ static nsi_status stabilized_p(NsiHandle* h, const FieldView& f, const StabConst
     stab_star_kernel<P, false><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks,
                                                                     h->star_ptr, h->star_word, Auu, G, rhs);
   if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
-  nsi_status st = check_launch("stab_star_kernel");
+  st = check_launch("stab_star_kernel");
   if (st) return st;
   if (h->long_rows > 0) {
     stab_rows_kernel<P><<<(h->long_rows + 63) / 64, 64, 0, s>>>(m, f, sc, Auu, G, rhs, h->long_list, h->long_ptr,
