@@ -75,7 +75,6 @@ static void free_handle(NsiHandle* h) {
   cudaFree(h->long_inc);
   cudaFree(h->exact_ptr);
   cudaFree(h->exact_inc);
-  cudaFree(h->star_ptr);
   cudaFree(h->star_word);
   cudaFree(h->star_task);
   cudaFree(h->fan);
@@ -749,20 +748,21 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if ((st = dev_upload(h, &h->exact_ptr, exact_ptr.data(), exact_ptr.size(), s))) return st;
     if ((st = dev_upload(h, &h->exact_inc, exact_inc.data(), exact_inc.size(), s))) return st;
   }
-  // the stabilised block's row kernel: star offsets and words, and warp
-  // tasks of one row (up to 32 entries, or a long row, which the kernel
-  // skips) or two consecutive rows of at most 16 entries each
-  std::vector<int32_t> star_ptr_h, star_task;
+  // the stabilised block's row kernel: star words and warp tasks of one row
+  // (up to 32 entries, or a long row, which the kernel skips) or two
+  // consecutive rows of at most 16 entries each
+  std::vector<int4> star_task;
   if (h->gather_ok) {
-    star_ptr_h.assign(inc_ptr.begin(), inc_ptr.end());
     for (int64_t i = 0; i < n;) {
-      star_task.push_back((int32_t)i);
       const bool pair = i + 1 < n && !is_long[i] && !is_long[i + 1] && row_len[i] <= 16 && row_len[i + 1] <= 16;
-      i += pair ? 2 : 1;
+      const int64_t e = i + (pair ? 2 : 1);
+      const int d0 = is_long[i] ? 0 : diag[i], d1 = pair ? diag[i + 1] : 0;
+      star_task.push_back(int4{(int)i, (int)rp64[i], (int)rp64[i + 1], (int)rp64[e]});
+      star_task.push_back(int4{(int)inc_ptr[i], (int)inc_ptr[i + 1], (int)inc_ptr[e],
+                               d0 | (d1 << 8) | ((int)(e - i) << 16) | ((is_long[i] ? 1 : 0) << 24)});
+      i = e;
     }
-    star_task.push_back((int32_t)n);
-    h->n_star_tasks = (int64_t)star_task.size() - 1;
-    if ((st = dev_upload(h, &h->star_ptr, star_ptr_h.data(), star_ptr_h.size(), s))) return st;
+    h->n_star_tasks = (int64_t)star_task.size() / 2;
     if ((st = dev_upload(h, &h->star_word, star.data(), star.size(), s))) return st;
     if ((st = dev_upload(h, &h->star_task, star_task.data(), star_task.size(), s))) return st;
   }

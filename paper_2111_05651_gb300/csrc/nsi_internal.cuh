@@ -194,10 +194,12 @@ struct NsiHandle {
   // the stabilised block's row kernel: every row's star as row positions of
   // each element's other three nodes (five bits each, the row's node and the
   // three in a positively oriented order), and its warp tasks (one row, or two
-  // consecutive rows of at most 16 entries); long rows are left out
-  int32_t* star_ptr = nullptr;    // [n + 1] into star_word
+  // consecutive rows of at most 16 entries), each described by two int4:
+  // {first row, CSR start of the first row, of the second, end} and
+  // {star start of the first row, of the second, end, diagonal positions |
+  // rows << 16 | long << 24}
   uint16_t* star_word = nullptr;  // [incidences]
-  int32_t* star_task = nullptr;   // [n_star_tasks + 1] first row of every task
+  int4* star_task = nullptr;      // [2 n_star_tasks]
   int64_t n_star_tasks = 0;
   nsi::GatherPlan plan;         // the launch plan in use
   nsi::GatherPlan plans[4];     // every rows-per-block candidate that fits shared memory

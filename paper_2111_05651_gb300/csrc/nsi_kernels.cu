@@ -2200,11 +2200,9 @@ constexpr int STAR_WARPS = 4;  // warps (tasks) per block
 // Long rows (more than 32 entries, or a star the row-gather encoder could
 // not cover) are single-row tasks this kernel skips.
 template <int P, bool DEBUG>
-__global__ void __launch_bounds__(32 * STAR_WARPS) stab_star_kernel(MeshView m, FieldView f, StabConst sc,
-                                                                    const int32_t* __restrict__ tasks, int64_t ntasks,
-                                                                    const int32_t* __restrict__ star_ptr,
-                                                                    const uint16_t* __restrict__ star_word,
-                                                                    void* Auu, void* Gv, void* rhs) {
+__global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_star_kernel(
+    MeshView m, FieldView f, StabConst sc, const int4* __restrict__ tasks, int64_t ntasks,
+    const uint16_t* __restrict__ star_word, void* Auu, void* Gv, void* rhs) {
   extern __shared__ __align__(16) unsigned char smem[];
   using T = typename Prec<P>::T;
   using Out = typename Prec<P>::Out;
@@ -2218,22 +2216,23 @@ __global__ void __launch_bounds__(32 * STAR_WARPS) stab_star_kernel(MeshView m, 
   T4<T>* el = reinterpret_cast<T4<T>*>(ws + StarSmem<P>::el());
   unsigned* mk = reinterpret_cast<unsigned*>(ws + StarSmem<P>::mask());  // [3 nodes][2 words][32 lanes]
 
-  const int32_t r0 = tasks[task];
-  const int nrow = tasks[task + 1] - r0;  // 1 or 2
-  // the stars' bounds and the first chunk's words, loaded ahead of the rows'
-  // records (independent of them)
-  const int64_t s0 = star_ptr[r0], s1 = star_ptr[r0 + 1], s2 = nrow == 2 ? star_ptr[r0 + 2] : s1;
+  // the task's rows, CSR and star bounds and diagonal positions in one
+  // 32-byte descriptor; long rows are left to the per-row kernel
+  const int4 ta = tasks[2 * task], tb = tasks[2 * task + 1];
+  if ((tb.w >> 24) & 1) return;  // warp-uniform
+  const int nrow = (tb.w >> 16) & 3;  // 1 or 2
+  const int64_t s0 = tb.x, s1 = tb.y, s2 = tb.z;
   const int nel = (int)(s2 - s0);
+  // the first chunk's star words, loaded ahead of the rows' records
   unsigned wpre[2];
 #pragma unroll
   for (int hf = 0; hf < 2; ++hf) wpre[hf] = hf * 32 + lane < nel ? star_word[s0 + hf * 32 + lane] : 0u;
   const int width = nrow == 2 ? 16 : 32;
   const int seg = nrow == 2 ? lane >> 4 : 0;
   const int q = lane - seg * width;  // this lane's position in its row
-  const int64_t i = r0 + seg;
-  const int32_t rs = m.row_ptr[i], len = m.row_ptr[i + 1] - rs;
-  const int dp = m.diag_pos[i];
-  if (nrow == 1 && (len > 32 || dp == DIAG_LONG)) return;  // a long row: the per-row kernel's
+  const int64_t i = (int64_t)ta.x + seg;
+  const int32_t rs = seg ? ta.z : ta.y, len = (seg || nrow == 1 ? ta.w : ta.z) - rs;
+  const int dp = seg ? (tb.w >> 8) & 255 : tb.w & 255;
   if (DEBUG && (len > width || (len > 0 && dp >= len))) {
     atomicOr(m.err, ERR_STAR);
     return;
@@ -3497,11 +3496,11 @@ static nsi_status stabilized_p(NsiHandle* h, const FieldView& f, const StabConst
   const int64_t grid = (h->n_star_tasks + STAR_WARPS - 1) / STAR_WARPS;
   if (h->ev_start) NSI_CUDA(cudaEventRecord(h->ev_start, s));
   if (h->debug)
-    stab_star_kernel<P, true><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks, h->star_ptr,
+    stab_star_kernel<P, true><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks,
                                                                    h->star_word, Auu, G, rhs);
   else
     stab_star_kernel<P, false><<<grid, 32 * STAR_WARPS, smem, s>>>(m, f, sc, h->star_task, h->n_star_tasks,
-                                                                    h->star_ptr, h->star_word, Auu, G, rhs);
+                                                                    h->star_word, Auu, G, rhs);
   if (h->ev_stop) NSI_CUDA(cudaEventRecord(h->ev_stop, s));
   st = check_launch("stab_star_kernel");
   if (st) return st;
