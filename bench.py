@@ -89,10 +89,13 @@ def stab_times(mesh, u, precs, steps, warmup, flush, stream, rows=None):
         ms, kms = time_steps(asm, fn, steps if prec != "fp64" else max(3, min(steps, 5)), warmup, flush, stream)
         km = statistics.mean(kms)
         nb = stab_bytes(E, n, asm.nnz, prec)
+        info = asm.info()
         rec = {"ms": statistics.mean(ms), "kernel_ms": km, "elements_per_s": E / (statistics.mean(ms) * 1e-3),
                "algorithmic_bytes": nb, "achieved_gbs": nb / (km * 1e-3) / 1e9,
-               "roofline_frac": nb / (km * 1e-3) / 1e9 / peak, "fan_kernel": bool(asm.info().fan_ok),
-               "launches_per_step": 2 if asm.info().fan_ok else 1}
+               "roofline_frac": nb / (km * 1e-3) / 1e9 / peak, "kernel": "stab_star_kernel",
+               # pack, the row kernel, then the per-row kernel for long rows and
+               # (mixed modes) for the rows of badly shaped elements, if any
+               "launches_per_step": 2 + (info.long_rows > 0) + (prec != "fp64" and info.exact_rows > 0)}
         if rows is not None:
             uo = u if prec == "fp64" else u.astype(np.float32).astype(np.float64)
             ref = oracle.assemble_stabilized_rows(mesh.coord, mesh.lnods, uo, rows, None, meshgen.RHO, meshgen.MU,
