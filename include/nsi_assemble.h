@@ -42,13 +42,15 @@
  *      NSI_MIXED_F32_ACC64 u, u_n: float;   A, G, rhs: double.  Gathers and
  *                          element arithmetic in float (coordinates kept as
  *                          float hi/lo pairs so edge vectors keep ~48 bits);
- *                          A, the lumped mass and the RHS accumulated as
- *                          compensated float pairs (about 48 significant
- *                          bits; A's diagonal is the mass minus its row's
- *                          other entries), G in float (its element terms are
- *                          float products; about 1e-7 of the row's largest
- *                          entry); stored as double.  The element-centric
- *                          modes (colour, atomic) add in double.
+ *                          A's off-diagonal entries and G summed in float
+ *                          (each the few element terms of one edge, float
+ *                          products: about 1e-7 of the row's largest entry);
+ *                          A's diagonal (the lumped mass minus its row's
+ *                          other entries, where the row's terms cancel), the
+ *                          lumped mass and the RHS as compensated float
+ *                          pairs (about 48 significant bits); stored as
+ *                          double.  The element-centric modes (colour,
+ *                          atomic) add in double.
  *      NSI_MIXED_F32_ACC32 u, u_n: float;   A, G, rhs: float.
  *  - Outputs are OVERWRITTEN by every assemble call (the call defines every
  *    entry; no prior zeroing is needed).

@@ -133,9 +133,9 @@ __host__ __device__ inline GatherSmem gather_smem(int precision, int R, int W, i
   g.L = L;
   g.S = S;
   g.tb = precision == NSI_FP64 ? 8 : 4;
-  // accumulator bytes per slot: FP64 (A, G_x, G_y, G_z) doubles; mixed64 a
-  // float4 (G_x, G_y, G_z, A leading part) + A's error term; mixed32 a float4
-  g.ab = precision == NSI_FP64 ? 32 : precision == NSI_MIXED_F32_ACC64 ? 20 : 16;
+  // accumulator bytes per slot: FP64 (A, G_x, G_y, G_z) doubles; the mixed
+  // modes a float4 (G_x, G_y, G_z, A)
+  g.ab = precision == NSI_FP64 ? 32 : 16;
   if (step) g.ab = precision == NSI_FP64 ? 32 : 16;
   g.xs = 0;
   g.ob = precision == NSI_MIXED_F32_ACC32 ? 4 : 8;

@@ -610,42 +610,30 @@ struct AccSmem<NSI_MIXED_F32_ACC32> {
     return {v.w, v.x, v.y, v.z};
   }
 };
-// mixed64: the A value as a compensated pair (leading part with G in one
-// float4, error term in its own array), the pressure-gradient sums in plain
-// float.  G's element terms -c_i / 24 are float products, and its sums over
-// the ~5 elements of an edge carry a few float roundings (about 1e-7 of the
-// row's largest entry); A, whose diagonal is the lumped mass minus the row's
-// other entries (the row sums of the convection and viscous terms cancel),
-// keeps the compensated sum (about 48 significant bits).
+// mixed64: float slots (G_x, G_y, G_z, A) as mixed32.  An off-diagonal entry
+// sums the ~5 element terms of its edge (float products), so its float sum
+// carries a few roundings of those terms; the cancellation is in the
+// diagonal, the lumped mass minus the row's other entries, which row_sums
+// forms as a compensated sum (TwoSum over the row's entries, about 48
+// significant bits).  The diagonal's error term stays in a register of the
+// row's thread (dlo) until the write-out converts the pair to double.
 template <>
 struct AccSmem<NSI_MIXED_F32_ACC64> {
-  float4* __restrict__ hi;  // (G_x, G_y, G_z, A leading part)
-  float* __restrict__ lo;   // A error term
-  __device__ __forceinline__ AccSmem(unsigned char* p, size_t N)
-      : hi(reinterpret_cast<float4*>(p)), lo(reinterpret_cast<float*>(p) + 4 * N) {}
-  __device__ __forceinline__ void zero(int k) {
-    hi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    lo[k] = 0.f;
-  }
+  float4* __restrict__ hi;  // (G_x, G_y, G_z, A)
+  float dlo = 0.f;          // error term of this thread's diagonal A (set())
+  __device__ __forceinline__ AccSmem(unsigned char* p, size_t) : hi(reinterpret_cast<float4*>(p)) {}
+  __device__ __forceinline__ void zero(int k) { hi[k] = make_float4(0.f, 0.f, 0.f, 0.f); }
   struct Slot {
-    float2 g, r;  // (G_x, G_y), (G_z, A leading part)
-    float l;      // A error term
+    float2 g, r;  // (G_x, G_y), (G_z, A)
   };
   __device__ __forceinline__ Slot load1(int k) const {
     const float4 h = hi[k];
-    return {make_float2(h.x, h.y), make_float2(h.z, h.w), lo[k]};
+    return {make_float2(h.x, h.y), make_float2(h.z, h.w)};
   }
-  __device__ __forceinline__ void store1(int k, const Slot& v) {
-    hi[k] = make_float4(v.g.x, v.g.y, v.r.x, v.r.y);
-    lo[k] = v.l;
-  }
-  // G plain, A by TwoSum on its lane of the (G_z, A) pair
+  __device__ __forceinline__ void store1(int k, const Slot& v) { hi[k] = make_float4(v.g.x, v.g.y, v.r.x, v.r.y); }
   static __device__ __forceinline__ void add(Slot& s, float2 gxy, float2 gz_a) {
     s.g = add2(s.g, gxy);
-    const float2 t = add2(s.r, gz_a);
-    const float bb = t.y - s.r.y;
-    s.l += (s.r.y - (t.y - bb)) + (gz_a.y - bb);
-    s.r = t;
+    s.r = add2(s.r, gz_a);
   }
   // sums over the row's slots, the diagonal's included (still zero): A
   // compensated, G plain (r[0]: A, r[1..3]: G_x..G_z with zero error terms)
@@ -658,7 +646,7 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
       g = add2(g, make_float2(h.x, h.y));
       const float2 t2 = add2(za, make_float2(h.z, h.w));
       const float bb = t2.y - za.y;
-      al += ((za.y - (t2.y - bb)) + (h.w - bb)) + lo[k];
+      al += (za.y - (t2.y - bb)) + (h.w - bb);
       za = t2;
     }
     r[0].hi = za.y; r[0].lo = al;
@@ -666,10 +654,10 @@ struct AccSmem<NSI_MIXED_F32_ACC64> {
     r[2].hi = g.y; r[2].lo = 0.f;
     r[3].hi = za.x; r[3].lo = 0.f;
   }
-  // the diagonal: A as a pair, G as the leading parts
+  // the diagonal: A's leading part and G in the slot, A's error term kept
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC64>* r) {
     hi[k] = make_float4(r[1].hi, r[2].hi, r[3].hi, r[0].hi);
-    lo[k] = r[0].lo;
+    dlo = r[0].lo;
   }
 };
 template <>
@@ -1155,7 +1143,8 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
     }
   } else {
     // mixed64: one staging round.  Every thread stages its own row's values
-    // in CSR order -- A as its (leading, error) pair and the three G floats,
+    // in CSR order -- A as a (leading, error) pair (the error term is the
+    // diagonal's, zero elsewhere) and the three G floats,
     // G_z in the half of nb1 that the next block's column indices (copied in
     // under this write-out by the persistent grid) leave free -- then the
     // block converts them to double and streams them out coalesced (the
@@ -1169,7 +1158,7 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
 #pragma unroll 4
       for (int q = 0, k = t; q < len; ++q, k += R) {
         const float4 h = acc.hi[k];
-        pa[lb + q] = make_float2(h.w, acc.lo[k]);
+        pa[lb + q] = make_float2(h.w, q == b.dp ? acc.dlo : 0.f);
         gx[lb + q] = h.x;
         gy[lb + q] = h.y;
         gz[lb + q] = h.z;

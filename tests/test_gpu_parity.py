@@ -77,9 +77,10 @@ def test_integer_valued_assembly_is_exact(precision, scatter):
     rho = 120 (rho/120 = 1), mu = 0 and dt = 5 / 2^20 (lumped mass rho|T|/(4 dt)
     = 2^20 per element): every element term of A and of the RHS is an integer
     exact in float (the convection terms below 2^22), while the diagonal
-    entries, the lumped mass minus the row's other entries, need up to 26 bits.
-    FP64 and the compensated float-pair sums of mixed64 with their conversion
-    to double must then give the exact integers: the oracle's values rounded to
+    entries, the lumped mass minus the row's other entries, need up to 26 bits
+    (the off-diagonal sums stay below 2^24, exact in float).  FP64 and
+    mixed64's compensated float-pair diagonal, lumped mass and RHS with their
+    conversion to double must then give the exact integers: the oracle's values rounded to
     the nearest integer (its 4-point quadrature leaves them within 1e-3 of
     one).  The cached-geometry time step (A_static + C(u)) must give them too."""
     N = 7
