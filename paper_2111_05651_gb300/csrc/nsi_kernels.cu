@@ -507,28 +507,6 @@ __device__ __forceinline__ double float_double(float x) {
   const unsigned hi = (a < 0x00800000u ? 0u : (a >> 3) + (896u << 20)) | (u & 0x80000000u);
   return __hiloint2double((int)hi, a < 0x00800000u ? 0 : (int)(u << 29));
 }
-// The double nearest hi + lo for a renormalised float pair (|lo| <= ulp(hi) /
-// 2), from the bit patterns: the double of |hi| plus lo, with hi's sign taken
-// out, counted in units of that double's last place, k = round(lo 2^(52-E))
-// for hi's exponent E (|k| <= 2^28; the float product is exact and the
-// conversion rounds to nearest even, as do the low 29 bits of |hi|'s double,
-// all zero); when |hi| is a power of two and lo points below it, the sum lies
-// in the binade below, whose units are half as large (k doubled); hi's sign
-// is set last.  Exact for hi = lo = 0 and for hi of exponent field 53..254;
-// `slow` is set for the rest (hi below 2^-74, infinite or NaN), which the
-// caller converts another way.
-__device__ __forceinline__ double pair_double_fast(float hi, float lo, bool& slow) {
-  const unsigned u = __float_as_uint(hi);
-  const unsigned a = u & 0x7fffffffu;
-  const unsigned eh = a >> 23;
-  slow |= (eh - 53u > 201u) & (a != 0u);
-  const float ls = __uint_as_float(__float_as_uint(lo) ^ (u & 0x80000000u));
-  const unsigned below = ((a & 0x007fffffu) == 0u && ls < 0.0f) ? 1u : 0u;
-  const int k = __float2int_rn(ls * __uint_as_float(((306u + below - eh) & 0xffu) << 23));
-  const unsigned long long mag = a == 0u ? 0ull : ((unsigned long long)a << 29) + (896ull << 52);
-  return __longlong_as_double((long long)((mag + (unsigned long long)(long long)k) |
-                                          ((unsigned long long)(u & 0x80000000u) << 32)));
-}
 // the double nearest hi + lo of a pair with a finite hi: renormalised first
 // (Fast2Sum)
 __device__ __forceinline__ double pair_double(float hi, float lo) {
@@ -1142,52 +1120,53 @@ __device__ __forceinline__ void gather_writeout(const MeshView& m, const OutView
       dst[3][k] = stage[3 * L + k];
     }
   } else {
-    // mixed64: one staging round.  Every thread stages its own row's values
-    // in CSR order -- A as a (leading, error) pair (the error term is the
-    // diagonal's, zero elsewhere) and the three G floats,
-    // G_z in the half of nb1 that the next block's column indices (copied in
-    // under this write-out by the persistent grid) leave free -- then the
-    // block converts them to double and streams them out coalesced (the
-    // conversions spread evenly over the threads).  A pair whose leading part
-    // is infinite, NaN or below 2^-74 is converted again by a rare pass.
-    float2* pa = reinterpret_cast<float2*>(smem + lay.nb0());
-    float* gx = reinterpret_cast<float*>(smem + lay.nb0()) + 2 * L;
+    // mixed64: one staging round.  Every thread stages its own row's float
+    // values in CSR order -- A and G_x, G_y in nb0, G_z in the half of nb1
+    // that the next block's column indices (copied in under this write-out by
+    // the persistent grid) leave free -- then the block converts them to
+    // double exactly and streams them out coalesced (the conversions spread
+    // evenly over the threads); an infinite, NaN or subnormal A is converted
+    // again by a rare pass.  Last, each row's thread overwrites its diagonal
+    // with the double of its compensated pair (leading part in the slot, error
+    // term in dlo).
+    float* sa = reinterpret_cast<float*>(smem + lay.nb0());
+    float* gx = sa + L;
     float* gy = gx + L;
     float* gz = reinterpret_cast<float*>(smem + lay.nb1()) + lay.N();
     if (t < nrows) {
 #pragma unroll 4
       for (int q = 0, k = t; q < len; ++q, k += R) {
         const float4 h = acc.hi[k];
-        pa[lb + q] = make_float2(h.w, q == b.dp ? acc.dlo : 0.f);
+        sa[lb + q] = h.w;
         gx[lb + q] = h.x;
         gy[lb + q] = h.y;
         gz[lb + q] = h.z;
       }
       for (int q = 0; q < b.zl; ++q) {  // a long row: its slice zeroed here, computed later
-        pa[lb + q] = make_float2(0.f, 0.f);
+        sa[lb + q] = 0.f;
         gx[lb + q] = gy[lb + q] = gz[lb + q] = 0.f;
       }
     }
     __syncthreads();
     bool slow = false;
     for (int k = t; k < L; k += R) {
-      const float2 a = pa[k];
-      const float sh = a.x + a.y;  // Fast2Sum: |error| <= ulp(leading) / 2
-      const float sl = a.y - (sh - a.x);
-      dst[0][k] = pair_double_fast(sh, sl, slow);
+      const float a = sa[k];
+      slow |= special_float(a);
+      dst[0][k] = float_double(a);
       dst[1][k] = float_double(gx[k]);
       dst[2][k] = float_double(gy[k]);
       dst[3][k] = float_double(gz[k]);
     }
     if (__syncthreads_or(slow)) {  // block-uniform and rare
       for (int k = t; k < L; k += R) {
-        const float2 a = pa[k];
-        const float sh = a.x + a.y;
-        const float sl = a.y - (sh - a.x);
-        bool sk = false;
-        (void)pair_double_fast(sh, sl, sk);
-        if (sk) dst[0][k] = nonfinite_bits(a.x) ? nonfinite_double(a.x) : (double)sh + (double)sl;
+        const float a = sa[k];
+        if (special_float(a)) dst[0][k] = nonfinite_bits(a) ? nonfinite_double(a) : (double)a;
       }
+      __syncthreads();
+    }
+    if (t < nrows && len > 0) {
+      const float hd = acc.hi[b.dp * R + t].w;
+      dst[0][lb + b.dp] = nonfinite_bits(hd) ? nonfinite_double(hd) : pair_double(hd, acc.dlo);
     }
   }
 }
