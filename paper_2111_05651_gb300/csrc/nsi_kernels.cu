@@ -2252,9 +2252,9 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
   // 2-3. elements in chunks of 64, then the entries' sums
   const int dp0 = __shfl_sync(FULL, dp, 0), dp1 = __shfl_sync(FULL, dp, 16);
   const int len0 = __shfl_sync(FULL, len, 0), len1 = __shfl_sync(FULL, len, 16);
-  Acc<P> sA, sD;
-  sA.zero();
-  sD.zero();
+  // an entry's sums (the few elements of its edge) in plain T; the row
+  // totals below are compensated in mixed64
+  T sA = T(0), sD = T(0);
   T K[9], G[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int c = 0; c < 9; ++c) K[c] = T(0);
@@ -2317,8 +2317,8 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
         const int k = ((m1 >> e) & 1ull) ? 2 : ((m2 >> e) & 1ull) ? 3 : 1;
         const T4<T>* r = el + 5 * e;
         const T4<T> r0v = r[0], rk = r[k], r4 = r[4];
-        sA.add(rk.w);
-        sD.add(r4.y);
+        sA += rk.w;
+        sD += r4.y;
         const T kv = r0v.w, kd = r4.x;
         const T ri[3] = {r0v.x, r0v.y, r0v.z}, c[3] = {rk.x, rk.y, rk.z};
 #pragma unroll
@@ -2335,7 +2335,11 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
   }
 
   // 4. row totals (lanes without an off-diagonal entry hold zeros)
-  Acc<P> tA = sA, tD = sD;
+  Acc<P> tA, tD;
+  tA.zero();
+  tD.zero();
+  tA.add(sA);
+  tD.add(sD);
   T tK[9], tG[3];
 #pragma unroll
   for (int c = 0; c < 9; ++c) tK[c] = K[c];
@@ -2394,13 +2398,7 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
     } else {
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        if (c % 4 == 0) {
-          Acc<P> x = sA;
-          x.add(K[c]);
-          store_acc(A + c * m.nnz + g, x);
-        } else {
-          A[c * m.nnz + g] = (Out)K[c];
-        }
+        A[c * m.nnz + g] = (Out)(c % 4 == 0 ? sA + K[c] : K[c]);
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(G[c] * kg);
