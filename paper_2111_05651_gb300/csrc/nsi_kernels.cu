@@ -1217,6 +1217,9 @@ struct AccA<NSI_MIXED_F32_ACC32> {
   }
   __device__ __forceinline__ void set(int k, const Acc<NSI_MIXED_F32_ACC32>& r) { a[k].x = r.v; }
 };
+// mixed64: an off-diagonal entry of C(u) sums the few element terms of its
+// edge in plain float (its error term stays zero); the diagonal, minus the
+// row's other entries, is the compensated row sum (set() stores the pair).
 template <>
 struct AccA<NSI_MIXED_F32_ACC64> {
   float4* __restrict__ a;
@@ -1228,12 +1231,7 @@ struct AccA<NSI_MIXED_F32_ACC64> {
     return make_float2(v.x, v.y);
   }
   __device__ __forceinline__ void store1(int k, Slot v) { reinterpret_cast<float2*>(a + k)[0] = v; }
-  static __device__ __forceinline__ void add(Slot& s, float x) {
-    float sum, e;
-    two_sum(s.x, x, sum, e);
-    s.x = sum;
-    s.y += e;
-  }
+  static __device__ __forceinline__ void add(Slot& s, float x) { s.x += x; }
   __device__ __forceinline__ void row_sum(int t, int R, int len, Acc<NSI_MIXED_F32_ACC64>& r) const {
 #pragma unroll 4
     for (int q = 0, k = t; q < len; ++q, k += R) {
