@@ -2199,8 +2199,8 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
   const int64_t i = (int64_t)ta.x + seg;
   const int32_t rs = seg ? ta.z : ta.y, len = (seg || nrow == 1 ? ta.w : ta.z) - rs;
   const int dp = seg ? (tb.w >> 8) & 255 : tb.w & 255;
-  if (DEBUG && (len > width || (len > 0 && dp >= len))) {
-    atomicOr(m.err, ERR_STAR);
+  if (DEBUG && __any_sync(FULL, len > width || (len > 0 && dp >= len))) {  // warp-uniform
+    if (lane == 0) atomicOr(m.err, ERR_STAR);
     return;
   }
   const bool has = q < len;
@@ -2270,8 +2270,11 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
         const int edp = es ? dp1 : dp0;
         const unsigned w = c0 == 0 ? wpre[half] : star_word[s0 + t];
         const int pa = w & 31, pb = (w >> 5) & 31, pc = (w >> 10) & 31;
-        if (DEBUG && (pa >= (es ? len1 : len0) || pb >= (es ? len1 : len0) || pc >= (es ? len1 : len0)))
-          atomicOr(m.err, ERR_STAR);
+        const int elen = es ? len1 : len0;
+        if (DEBUG && (pa >= elen || pb >= elen || pc >= elen || elen > width)) {
+          atomicOr(m.err, ERR_STAR);  // the element is left out
+          continue;
+        }
         auto rd = [&](int l, int c) { return V3<T>{er[c * 32 + l], er[(c + 1) * 32 + l], er[(c + 2) * 32 + l]}; };
         const V3<T> d1 = rd(eb + pa, 0), d2 = rd(eb + pb, 0), d3 = rd(eb + pc, 0);
         const V3<T> u1 = rd(eb + pa, 3), u2 = rd(eb + pb, 3), u3 = rd(eb + pc, 3), ui = rd(eb + edp, 3);
