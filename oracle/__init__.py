@@ -8,7 +8,8 @@ double); this module compiles it with gcc on first use and wraps it for numpy.
 Array conventions (see ``nsi_oracle.c``): ``coord``, ``u``, ``un``, ``w`` are
 node-major float64 [n, 3]; ``lnods`` int32 [E, 4] 0-based; CSR ``row_ptr``
 int32 [n+1], ``col_idx`` int32 [nnz]; ``G`` float64 [3, nnz]; ``rhs`` float64
-[3, n].
+[3, n]; the stabilised velocity block ``Auu`` float64 [9, nnz], component
+3 i + j the (i, j) entry of every entry's 3x3 block.
 """
 from __future__ import annotations
 
