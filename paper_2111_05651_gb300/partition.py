@@ -15,7 +15,9 @@ adds them up at the node's owner:
       every entry and node value of its local assembly the place it goes: a
       position in its own rows, or a position in another rank's rows (then it
       is sent);
-  every call (``PartitionedAssembler.assemble``):
+  every call (``PartitionedAssembler.assemble``; ``assemble_stabilized`` for
+  the stabilised velocity block, whose entries carry twelve values -- the
+  nine components of the 3x3 block, then G -- instead of four):
     1. the local assembly (``nsi_assemble`` on the rank's sub-mesh);
     2. the values of the entries of rows owned by other ranks packed into one
        send buffer (``nsi_gather_values``, a library kernel);
@@ -27,10 +29,9 @@ adds them up at the node's owner:
        one call, so plain read-add-write, and the order of the sums is fixed:
        the result does not depend on timing).
 
-Each rank ends with A, G and rhs of the rows it owns, in the global
-numbering and pattern (``RankPlan.own_rows``, ``own_row_ptr``,
-``own_cols``).  The exchange sizes are fixed at setup; the buffers are
-allocated once.
+Each rank ends with A (or the stabilised Auu), G and rhs of the rows it
+owns, in the global numbering and pattern (``RankPlan.own_rows``,
+``own_row_ptr``, ``own_cols``).  The exchange sizes are fixed at setup.
 """
 from __future__ import annotations
 
@@ -204,10 +205,12 @@ class PartitionedAssembler:
 
     ``assemble(u_local)`` takes the velocities of the rank's nodes
     (``plan.nodes`` order, [3, n_r]) and returns (A [nnz_own], G [3, nnz_own],
-    rhs [3, n_own]) of the rows the rank owns, after the exchange; with
-    ``exchange_fn`` another transport than torch.distributed can move the
-    blocks (the single-GPU test passes the blocks between two ranks of one
-    process)."""
+    rhs [3, n_own]) of the rows the rank owns, after the exchange;
+    ``assemble_stabilized(u_local)`` does the same for the stabilised velocity
+    block (Auu [9, nnz_own], G, rhs: twelve values per interface entry
+    instead of four).  With ``exchange_fn`` another transport than
+    torch.distributed can move the blocks (the single-GPU test passes the
+    blocks between the ranks of one process)."""
 
     def __init__(self, plan: RankPlan, precision="mixed64", device=None):
         import torch
@@ -230,16 +233,49 @@ class PartitionedAssembler:
         self.dtype = self.asm.out_dtype
         self.dev = dev
 
+    @staticmethod
+    def _chunks(A, G):
+        """The entry-value arrays in chunks of at most four components (what
+        one nsi_gather_values / nsi_add_values call moves), as (first, rest,
+        count): (A, G_x, G_y, G_z) for the assembly; (Auu 0-3), (Auu 4-7),
+        (Auu 8, G_x, G_y, G_z) for the stabilised block."""
+        if A.dim() == 1:
+            return [(A, G, 4)]
+        return [(None, A[0:4], 4), (None, A[4:8], 4), (A[8], G, 4)]
+
+    def _gather(self, chunks, stride, idx):
+        import torch
+
+        from . import gather_values
+
+        parts = [gather_values(f, r, stride, idx, nc) for f, r, nc in chunks]
+        return parts[0] if len(parts) == 1 else torch.cat(parts, dim=1)
+
+    @staticmethod
+    def _add(chunks, stride, idx, vals):
+        from . import add_values
+
+        c0 = 0
+        for f, r, nc in chunks:
+            add_values(f, r, stride, idx, vals[:, c0:c0 + nc], nc)
+            c0 += nc
+
     def local(self, u_local, rho=1.0, mu=1e-3, dt=1e-2):
         """Step 1: the local assembly."""
         return self.asm.assemble(u_local, rho=rho, mu=mu, dt=dt)
 
+    def local_stabilized(self, u_local, rho=1.0, mu=1e-3, dt=1e-2):
+        """Step 1 for the stabilised velocity block."""
+        return self.asm.assemble_stabilized(u_local, rho=rho, mu=mu, dt=dt)
+
     def pack(self, A, G, rhs):
-        """Step 2: per peer, the entries [count, 4] (A, G_x, G_y, G_z) and
-        node values [count, 3] of rows that peer owns."""
+        """Step 2: per peer, the entries [count, c] (A, G_x, G_y, G_z; or the
+        nine Auu components, then G) and node values [count, 3] of rows that
+        peer owns."""
         from . import gather_values
 
-        ent = [gather_values(A, G, self.plan.local_cols.size, s) for s in self.send_src]
+        chunks = self._chunks(A, G)
+        ent = [self._gather(chunks, self.plan.local_cols.size, s) for s in self.send_src]
         nod = [gather_values(None, rhs, self.plan.nodes.size, s, ncomp=3) for s in self.send_node_src]
         return ent, nod
 
@@ -247,27 +283,25 @@ class PartitionedAssembler:
         """Step 4: the owned rows -- own entries, then each peer's in rank order."""
         import torch
 
-        from . import add_values
+        from . import add_values, gather_values
 
         p = self.plan
-        from . import gather_values
-
-        oA = torch.zeros(p.nnz_own, dtype=self.dtype, device=self.dev)
+        oA = torch.zeros((p.nnz_own,) if A.dim() == 1 else (A.shape[0], p.nnz_own), dtype=self.dtype,
+                         device=self.dev)
         oG = torch.zeros(3, p.nnz_own, dtype=self.dtype, device=self.dev)
         orhs = torch.zeros(3, p.n_own, dtype=self.dtype, device=self.dev)
-        own_ent = gather_values(A, G, p.local_cols.size, self.keep_src)
+        own = self._chunks(oA, oG)
+        self._add(own, p.nnz_own, self.keep_dst, self._gather(self._chunks(A, G), p.local_cols.size, self.keep_src))
         own_nod = gather_values(None, rhs, p.nodes.size, self.keep_node_src, ncomp=3)
-        add_values(oA, oG, p.nnz_own, self.keep_dst, own_ent)
         add_values(None, orhs, p.n_own, self.keep_node_dst, own_nod, ncomp=3)
         for s in range(p.world):
             if s == p.rank:
                 continue
-            add_values(oA, oG, p.nnz_own, self.recv_dst[s], recv_ent[s])
+            self._add(own, p.nnz_own, self.recv_dst[s], recv_ent[s])
             add_values(None, orhs, p.n_own, self.recv_node_dst[s], recv_nod[s], ncomp=3)
         return oA, oG, orhs
 
-    def assemble(self, u_local, rho=1.0, mu=1e-3, dt=1e-2, exchange_fn=None, group=None):
-        A, G, rhs = self.local(u_local, rho, mu, dt)
+    def _exchange_and_finish(self, A, G, rhs, exchange_fn, group):
         ent, nod = self.pack(A, G, rhs)
         p = self.plan
         counts_ent = [int(x.size) for x in p.recv_dst]
@@ -278,6 +312,14 @@ class PartitionedAssembler:
         else:
             recv_ent, recv_nod = exchange_fn(ent, nod)
         return self.finish(A, G, rhs, recv_ent, recv_nod)
+
+    def assemble(self, u_local, rho=1.0, mu=1e-3, dt=1e-2, exchange_fn=None, group=None):
+        A, G, rhs = self.local(u_local, rho, mu, dt)
+        return self._exchange_and_finish(A, G, rhs, exchange_fn, group)
+
+    def assemble_stabilized(self, u_local, rho=1.0, mu=1e-3, dt=1e-2, exchange_fn=None, group=None):
+        Auu, G, rhs = self.local_stabilized(u_local, rho, mu, dt)
+        return self._exchange_and_finish(Auu, G, rhs, exchange_fn, group)
 
     def close(self):
         self.asm.close()

@@ -57,3 +57,48 @@ def test_partitioned_assembly_matches_whole_mesh(precision, world):
         assert np.abs(orhs - grhs[:, p.own_rows]).max() <= tol * np.abs(grhs).max()
     for r in ranks:
         r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+@pytest.mark.parametrize("world", [2, 3])
+def test_partitioned_stabilized_block_matches_whole_mesh(precision, world):
+    """The stabilised velocity block over ranks (twelve values per interface
+    entry: the nine Auu components, then G): the owned rows of every rank
+    against the oracle's stabilised assembly of the whole mesh and the
+    library's single-mesh call, component by component."""
+    mesh, u = meshgen.config_mesh(N=8, jitter=0.15, numbering="random", seed=97)
+    plans = pt.build_plans(mesh.coord, mesh.lnods, world)
+    ranks = [pt.PartitionedAssembler(p, precision=precision) for p in plans]
+    local, packs = [], []
+    for r, p in zip(ranks, plans):
+        out = r.local_stabilized(torch.as_tensor(u[p.nodes].T.copy()), RHO, MU, DT)
+        local.append(out)
+        packs.append(r.pack(*out))
+    assert all(e.shape[1] == 12 for e in packs[0][0])
+    results = []
+    for s, r in enumerate(ranks):
+        recv_ent = [packs[q][0][s] for q in range(world)]
+        recv_nod = [packs[q][1][s] for q in range(world)]
+        results.append(r.finish(*local[s], recv_ent, recv_nod))
+    torch.cuda.synchronize()
+    whole = nsi.Assembler(mesh.coord, mesh.lnods, precision=precision)
+    wAuu, wG, wrhs = (t.double().cpu().numpy()
+                      for t in whole.assemble_stabilized(torch.as_tensor(u.T.copy()), rho=RHO, mu=MU, dt=DT))
+    whole.close()
+    uo = u if precision == "fp64" else u.astype(np.float32).astype(np.float64)
+    g_rp, g_ci, gAuu, gG, grhs = oracle.assemble_stabilized(mesh.coord, mesh.lnods, uo, None, RHO, MU, DT)
+    tol = TOL[precision]
+    for p, (oAuu, oG, orhs) in zip(plans, results):
+        oAuu, oG, orhs = oAuu.double().cpu().numpy(), oG.double().cpu().numpy(), orhs.double().cpu().numpy()
+        assert oAuu.shape == (9, p.nnz_own)
+        for k, i in enumerate(p.own_rows):
+            sl, ol = slice(g_rp[i], g_rp[i + 1]), slice(p.own_row_ptr[k], p.own_row_ptr[k + 1])
+            pairs = tuple((oAuu[c, ol], gAuu[c, sl], wAuu[c, sl]) for c in range(9)) + \
+                tuple((oG[d, ol], gG[d, sl], wG[d, sl]) for d in range(3))
+            for got, ref, lib in pairs:
+                scale = max(np.abs(ref).max(), 1e-300)
+                assert np.abs(got - ref).max() <= tol * scale
+                assert np.abs(got - lib).max() <= 2 * tol * scale
+        assert np.abs(orhs - grhs[:, p.own_rows]).max() <= tol * np.abs(grhs).max()
+    for r in ranks:
+        r.close()

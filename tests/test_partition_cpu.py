@@ -63,7 +63,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, stab=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     sys.path.insert(0, ROOT)
     import torch
@@ -74,51 +74,76 @@ def _rank(rank, world, port, q):
         mesh, u = _mesh()
         plan = pt.build_plans(mesh.coord, mesh.lnods, world)[rank]
         ul = u[plan.nodes]
-        _, _, A, G, rhs = oracle.assemble(plan.coord, plan.lnods, ul, None, RHO, MU, DT)
-        ent = [torch.as_tensor(np.c_[A[s_], G[:, s_].T]) for s_ in plan.send_src]  # [count, 4]
+        if stab:  # the stabilised block: nine Auu components per entry, then G
+            _, _, A, G, rhs = oracle.assemble_stabilized(plan.coord, plan.lnods, ul, None, RHO, MU, DT)
+        else:
+            _, _, A, G, rhs = oracle.assemble(plan.coord, plan.lnods, ul, None, RHO, MU, DT)
+        A = A.reshape(-1, A.shape[-1])  # [1 or 9, nnz]
+        ent = [torch.as_tensor(np.c_[A[:, s_].T, G[:, s_].T]) for s_ in plan.send_src]  # [count, 4 or 12]
         nod = [torch.as_tensor(rhs[:, s_].T.copy()) for s_ in plan.send_node_src]  # [count, 3]
         recv_ent = pt.exchange(ent, [x.size for x in plan.recv_dst])
         recv_nod = pt.exchange(nod, [x.size for x in plan.recv_node_dst])
-        oA = np.zeros(plan.nnz_own); oG = np.zeros((3, plan.nnz_own)); orhs = np.zeros((3, plan.n_own))
-        oA[plan.keep_dst] += A[plan.keep_src]
+        c = A.shape[0]
+        oA = np.zeros((c, plan.nnz_own)); oG = np.zeros((3, plan.nnz_own)); orhs = np.zeros((3, plan.n_own))
+        oA[:, plan.keep_dst] += A[:, plan.keep_src]
         oG[:, plan.keep_dst] += G[:, plan.keep_src]
         orhs[:, plan.keep_node_dst] += rhs[:, plan.keep_node_src]
         for s in range(world):
             if s == rank:
                 continue
             v, w = recv_ent[s].numpy(), recv_nod[s].numpy()
-            oA[plan.recv_dst[s]] += v[:, 0]
-            oG[:, plan.recv_dst[s]] += v[:, 1:].T
+            oA[:, plan.recv_dst[s]] += v[:, :c].T
+            oG[:, plan.recv_dst[s]] += v[:, c:].T
             orhs[:, plan.recv_node_dst[s]] += w.T
         q.put((rank, plan.own_rows, plan.own_row_ptr, oA, oG, orhs))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_gloo_exchange_gives_the_whole_mesh_assembly(world):
+def _run_ranks(world, stab):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, stab)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=300) for _ in range(world)]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    mesh, u = _mesh()
-    g_rp, g_ci, gA, gG, grhs = oracle.assemble(mesh.coord, mesh.lnods, u, None, RHO, MU, DT)
+    return res
+
+
+def _check_owned_rows(res, g_rp, gA, gG, grhs, n):
     seen = 0
     for rank, rows, rp, oA, oG, orhs in res:
         for k, i in enumerate(rows):
             sl = slice(g_rp[i], g_rp[i + 1])
             ol = slice(rp[k], rp[k + 1])
-            scale = max(np.abs(gA[sl]).max(), 1e-300)
-            assert np.abs(oA[ol] - gA[sl]).max() <= 1e-12 * scale
+            for c in range(gA.shape[0]):
+                scale = max(np.abs(gA[c, sl]).max(), 1e-300)
+                assert np.abs(oA[c, ol] - gA[c, sl]).max() <= 1e-12 * scale
             for d in range(3):
                 sg = max(np.abs(gG[d, sl]).max(), 1e-300)
                 assert np.abs(oG[d, ol] - gG[d, sl]).max() <= 1e-12 * sg
         assert np.abs(orhs - grhs[:, rows]).max() <= 1e-12 * np.abs(grhs).max()
         seen += rows.size
-    assert seen == mesh.n_nodes
+    assert seen == n
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_exchange_gives_the_whole_mesh_assembly(world):
+    res = _run_ranks(world, stab=False)
+    mesh, u = _mesh()
+    g_rp, g_ci, gA, gG, grhs = oracle.assemble(mesh.coord, mesh.lnods, u, None, RHO, MU, DT)
+    _check_owned_rows(res, g_rp, gA[None, :], gG, grhs, mesh.n_nodes)
+
+
+def test_gloo_exchange_gives_the_whole_mesh_stabilized_block():
+    """The stabilised block over two gloo ranks: twelve values per interface
+    entry (the nine Auu components, then G), the owned rows equal to the
+    whole mesh's stabilised assembly."""
+    res = _run_ranks(2, stab=True)
+    mesh, u = _mesh()
+    g_rp, g_ci, gAuu, gG, grhs = oracle.assemble_stabilized(mesh.coord, mesh.lnods, u, None, RHO, MU, DT)
+    _check_owned_rows(res, g_rp, gAuu, gG, grhs, mesh.n_nodes)
