@@ -194,3 +194,31 @@ def test_stabilized_cube100_sampled_rows(cube100, precision):
                 worst = max(worst, np.abs(G[d, s:e] - g[d]).max() / np.abs(g[d]).max())
             worst = max(worst, np.abs(rhs[:, r] - rh).max() / np.abs(rhs).max())
         assert worst <= TOL[precision], worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed64", "mixed32"])
+def test_stabilized_repeated_elements(precision):
+    """Two tetrahedra sharing a face, each listed 40 times: the stars hold 40
+    or 80 copies of a few triangles, which the row-gather walk encoder cannot
+    walk, so every row becomes a long row (the per-row double kernels of the
+    assembly and of the stabilised block) while the handle stays valid.  The
+    stabilised block and the Galerkin assembly against the oracle."""
+    coord = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0.6, 0.7, 0.8]], dtype=np.float64)
+    t1, t2 = [0, 1, 2, 3], [1, 2, 3, 4]
+    X = coord[t2]
+    if np.linalg.det(np.c_[np.ones(4), X]) < 0:
+        t2 = [1, 3, 2, 4]
+    lnods = np.array([t1] * 40 + [t2] * 40, dtype=np.int32)
+    u = np.random.default_rng(38).standard_normal((5, 3))
+    mesh = meshgen.Mesh(coord=coord, lnods=lnods, N=0)
+    check(mesh, u, precision)
+    asm = nsi.Assembler(coord, lnods, precision=precision)
+    A, G, rhs = asm.assemble(torch.as_tensor(u.T.copy()), rho=RHO, mu=MU, dt=DT)
+    torch.cuda.synchronize()
+    asm.close()
+    _, _, oA, oG, orhs = oracle.assemble(coord, lnods, vel_in(u, precision), None, RHO, MU, DT)
+    rp = oracle.pattern(5, lnods)[0]
+    assert row_scaled_err(rp, A.double().cpu().numpy(), oA) <= TOL[precision]
+    for d in range(3):
+        assert row_scaled_err(rp, G[d].double().cpu().numpy(), oG[d]) <= TOL[precision]
+        assert vec_scaled_err(rhs[d].double().cpu().numpy(), orhs[d]) <= TOL[precision]
