@@ -282,11 +282,13 @@ nsi_status nsi_assemble_nodal(NsiHandle* h, const NsiFields* f, void* rhs, void*
  * element order (deterministic); rows of more than 32 entries
  * (NsiInfo.long_rows) and, in the mixed modes, the rows touching badly shaped
  * elements (NsiInfo.exact_rows) are then computed by one double-precision
- * thread per row.  Precision as nsi_assemble; in NSI_MIXED_F32_ACC64 the
- * diagonal components are compensated float pairs, the six others and G
- * float sums.  The handle's scatter mode does not apply.  NSI_ERR_UNSUPPORTED
- * for meshes of more than 2^31 node-element incidences.  Requires mu > 0 (tau1 of an element at rest
- * is h^2 / (4 mu)), rho >= 0, dt > 0 (NSI_ERR_INVALID_ARG otherwise).
+ * thread per row.  Precision as nsi_assemble; in NSI_MIXED_F32_ACC64 an
+ * entry's values are float sums of its edge's elements, and the diagonal
+ * block (the lumped mass minus the row's other blocks) is formed from
+ * compensated float-pair row totals.  The handle's scatter mode does not
+ * apply.  NSI_ERR_UNSUPPORTED for meshes of more than 2^31 node-element
+ * incidences.  Requires mu > 0 (tau1 of an element at rest is h^2 / (4 mu)),
+ * rho >= 0, dt > 0 (NSI_ERR_INVALID_ARG otherwise).
  * Never allocates or synchronises.
  */
 nsi_status nsi_assemble_stabilized(NsiHandle* h, const NsiFields* f, void* Auu, void* G_val, void* rhs,

@@ -646,8 +646,9 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if (best_warps == 0) h->gather_ok = false;
     else h->plan = h->plans[chosen];
     // the persistent grid (next block's phase 0 under the current block's
-    // write-out) measured faster for mixed64 only: 0.505 against 0.545 ms at
-    // the 100^3 cube; mixed32 unchanged, FP64 slower (4.23 against 3.29 ms)
+    // write-out) measured faster for mixed64: 0.280 against 0.302 ms at the
+    // 100^3 cube; it did not help mixed32 and slowed FP64 (4.23 against
+    // 3.29 ms, on an earlier kernel)
     h->persistent = h->precision == NSI_MIXED_F32_ACC64;
   }
 
