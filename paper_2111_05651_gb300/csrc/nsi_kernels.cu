@@ -20,7 +20,18 @@
 //                   rhs), or the paper's per-node outputs
 //   step_persistent_kernel  the same as a persistent grid (mixed32)
 //   vjp_kernel      adjoint of R(u, mu) = A(u) u - b, element per thread
-//   residual_kernel R(u, mu) without the matrix
+//   residual_kernel R(u, mu) without the matrix (both with an exact
+//                   companion for badly shaped elements in double)
+//   exact_rows_kernel, long_rows_kernel  rows recomputed or computed per
+//                   thread in double: the mixed modes' rows of badly shaped
+//                   elements, and rows beyond the walk (more than 32 entries)
+//   stab_star_kernel  the stabilised velocity block (3x3 per CSR entry): one
+//                   warp per row or pair of rows, each element evaluated
+//                   once per row, entry sums from shared memory
+//   stab_rows_kernel  the stabilised block of listed rows, one thread per
+//                   row in double
+//   gather_values_kernel, add_values_kernel  pack / add the interface-row
+//                   values of the element-partition exchange
 //
 // Formulas: see the element-arithmetic comment in nsi_internal.cuh.
 #include <algorithm>
