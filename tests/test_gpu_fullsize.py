@@ -5,8 +5,9 @@ rows one by one (every element touching a sampled row, in element order) and
 the library's rows are compared to them; the CSR pattern is checked on the
 same rows and through the closed-form Kuhn nnz.  Workloads: the 100^3 cube
 (6 M tets, random numbering), the 200^3 cube (48 M tets) in RCM and random
-numbering with 5% noise and mu in {1e-2, 1e-4}, 64 batched cubes of 10..60
-hexes a side, and the 50^3 adjoint case.
+numbering with 5% noise and mu in {1e-2, 1e-4} (with the stabilised block at
+mu = 1e-4), 64 batched cubes of 10..60 hexes a side, and the 50^3 adjoint
+case.
 """
 import numpy as np
 import pytest
@@ -138,7 +139,7 @@ def test_cube200(name):
         check_rows(asm, out, mesh, vel_in(u, "mixed32"), rows, 1e-5, mu=1e-2)
         del out
     asm.close()
-    # mixed with compensated (FP64-class) accumulation, mu = 1e-4
+    # mixed64 (compensated sums where the row cancels; double outputs), mu = 1e-4
     asm = nsi.Assembler(mesh.coord, mesh.lnods, precision="mixed64")
     for scatter in ("gather", "atomic"):
         out = asm.assemble(ut, rho=RHO, mu=1e-4, dt=DT, scatter=scatter)
@@ -146,7 +147,21 @@ def test_cube200(name):
         check_rows(asm, out, mesh, vel_in(u, "mixed64"), rows, 1e-5, mu=1e-4)
         check_rows(asm, out, mesh, u, rows, 1e-5, mu=1e-4)
         del out
+    # the stabilised velocity block at the same size (convective regime)
+    Auu, G, rhs = (t.double().cpu().numpy() for t in asm.assemble_stabilized(ut, rho=RHO, mu=1e-4, dt=DT))
+    rp, ci = (t.cpu().numpy() for t in asm.pattern())
     asm.close()
+    ref = oracle.assemble_stabilized_rows(mesh.coord, mesh.lnods, vel_in(u, "mixed64"), rows, None, RHO, 1e-4, DT)
+    worst = 0.0
+    for r, (cols, blk, g, rh) in zip(rows, ref):
+        s_, e_ = rp[r], rp[r + 1]
+        np.testing.assert_array_equal(ci[s_:e_], cols)
+        for c in range(9):
+            worst = max(worst, np.abs(Auu[c, s_:e_] - blk[c]).max() / np.abs(blk[c]).max())
+        for d in range(3):
+            worst = max(worst, np.abs(G[d, s_:e_] - g[d]).max() / np.abs(g[d]).max())
+        worst = max(worst, np.abs(rhs[:, r] - rh).max() / np.abs(rhs).max())
+    assert worst <= 1e-5, worst
 
 
 def test_batch64_batched_equals_single_and_oracle():
