@@ -25,3 +25,24 @@ def test_cube8_summary_unchanged():
             assert abs(g - r) <= 1e-13 * s
     for p, v in ref["A_at"].items():
         assert got["A_at"][p] == pytest.approx(v, rel=1e-13, abs=1e-18)
+
+
+def test_cube8_stabilized_summary_unchanged():
+    """The stabilised oracle's committed summary: component sums (the
+    diagonal components sum to rho/dt times the cube's volume, 100, since
+    every other term annihilates constants), absolute sums, five entries'
+    blocks and one element's tau1, tau2."""
+    from tests.golden.make_golden import stab_summary
+
+    with open(os.path.join(HERE, "golden", "cube8_stab_oracle.json")) as f:
+        ref = json.load(f)
+    got = stab_summary()
+    assert got["nnz"] == ref["nnz"]
+    for c in range(9):
+        assert abs(got["Auu_sum"][c] - ref["Auu_sum"][c]) <= 1e-13 * ref["Auu_abs_sum"][c]
+        assert got["Auu_abs_sum"][c] == pytest.approx(ref["Auu_abs_sum"][c], rel=1e-13)
+    for c in (0, 4, 8):
+        assert ref["Auu_sum"][c] == pytest.approx(100.0, rel=1e-13)
+    for p, v in ref["Auu_at"].items():
+        assert got["Auu_at"][p] == pytest.approx(v, rel=1e-13, abs=1e-18)
+    assert got["tau_element0"] == pytest.approx(ref["tau_element0"], rel=1e-14)
