@@ -66,7 +66,7 @@ def stab_bytes(E, n, nnz, precision):
     return 16 * E + n * (3 * sx + 3 * su) + 4 * (n + 1) + 4 * nnz + so * 12 * nnz + so * 3 * n
 
 
-def stab_times(mesh, u, precs, steps, warmup, flush, stream, rows=None):
+def stab_times(mesh, u, precs, steps, warmup, flush, stream, rows=None, sampler=None):
     """Per precision: ms per nsi_assemble_stabilized call and of its main kernel
     (L2 flushed before every step), elements/s, the HBM roofline of the kernel
     and the largest row-scaled error of sampled rows against the oracle."""
@@ -86,7 +86,11 @@ def stab_times(mesh, u, precs, steps, warmup, flush, stream, rows=None):
                torch.empty(3, asm.nnz, dtype=asm.out_dtype, device="cuda"),
                torch.empty(3, n, dtype=asm.out_dtype, device="cuda"))
         fn = lambda: asm.assemble_stabilized(ut, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT, out=out)  # noqa
+        if sampler is not None and prec == precs[0]:
+            sampler.mark("t0")
         ms, kms = time_steps(asm, fn, steps if prec != "fp64" else max(3, min(steps, 5)), warmup, flush, stream)
+        if sampler is not None and prec == precs[0]:
+            sampler.mark("t1")
         km = statistics.mean(kms)
         nb = stab_bytes(E, n, asm.nnz, prec)
         info = asm.info()
@@ -134,7 +138,7 @@ def run_stab(args, world, rank, local):
     sampler.start()
     barrier(world)
     res = stab_times(mesh, u, precs, args.steps, args.warmup, lambda: flush_buf.fill_(1),
-                     torch.cuda.current_stream(), rows)
+                     torch.cuda.current_stream(), rows, sampler)
     barrier(world)
     clocks = sampler.stop()
     m = res[args.precision]
@@ -822,7 +826,14 @@ def run_step(args, world, rank, local):
         fn = lambda: asm.assemble_convective(ut, A_static, rho=meshgen.RHO, mu=meshgen.MU, dt=meshgen.DT,  # noqa
                                              out=out)
         steps = args.steps if prec == "mixed64" else max(3, min(args.steps, 20))
+        sampler = ClockSampler(local) if prec == "mixed64" else None
+        if sampler:
+            sampler.start()
+            sampler.mark("t0")
         t_step, t_kern = time_steps(asm, fn, steps, args.warmup, lambda: flush_buf.fill_(1), stream)
+        if sampler:
+            sampler.mark("t1")
+        clocks = sampler.stop() if sampler else None
         ms, kms = float(np.mean(t_step)), float(np.mean(t_kern))
         # sampled rows of A and rhs against the oracle's full assembly
         u_in = u if prec == "fp64" else u.astype(np.float32).astype(np.float64)
@@ -836,6 +847,8 @@ def run_step(args, world, rank, local):
         nb = step_bytes(E, n, asm.nnz, prec)
         res[prec] = {"ms": ms, "kernel_ms": kms, "elements_per_s": E / (ms * 1e-3), "max_rel_err": float(err),
                      "algorithmic_bytes": nb, "achieved_gbs": nb / (kms * 1e-3) / 1e9}
+        if clocks is not None:
+            res[prec]["clocks"] = clocks
         asm.close()
     ms = allreduce_max(res["mixed64"]["ms"], world)
     if rank == 0:
@@ -852,6 +865,7 @@ def run_step(args, world, rank, local):
                                        "traffic": read_traffic("step_kernel", "cube100", "mixed64"), "kernel": "step_kernel",
                                        "algorithmic_bytes": m["algorithmic_bytes"], "kernel_ms": m["kernel_ms"],
                                        "peak_source": src},
+                          "clocks": m.pop("clocks", None), "gpu_launches": args.steps * 2,  # pack + step kernel
                           "max_rel_err": m["max_rel_err"], "modes": res}), flush=True)
 
 
