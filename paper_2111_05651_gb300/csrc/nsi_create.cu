@@ -646,10 +646,10 @@ static nsi_status build(NsiHandle* h, const NsiMesh* m, cudaStream_t s) {
     if (best_warps == 0) h->gather_ok = false;
     else h->plan = h->plans[chosen];
     // the persistent grid (next block's phase 0 under the current block's
-    // write-out) measured faster for mixed64: 0.280 against 0.302 ms at the
-    // 100^3 cube; it did not help mixed32 and slowed FP64 (4.23 against
-    // 3.29 ms, on an earlier kernel)
-    h->persistent = h->precision == NSI_MIXED_F32_ACC64;
+    // write-out) measured faster for the mixed modes: mixed64 0.280 against
+    // 0.302 ms, mixed32 0.228 against 0.239 ms at the 100^3 cube; it slowed
+    // FP64 (4.23 against 3.29 ms, on an earlier kernel)
+    h->persistent = h->precision != NSI_FP64;
   }
 
   // 7b. badly shaped elements (mixed modes): a float determinant of an
