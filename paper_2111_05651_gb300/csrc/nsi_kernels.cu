@@ -2169,10 +2169,13 @@ constexpr int STAR_WARPS = 4;  // warps (tasks) per block
 //  3. Each off-diagonal entry lane adds, in element order, the records of its
 //     masked elements: A + S, K += kv c_k x c_i + kd c_i x c_k, G's c_i sum and
 //     det for the lumped mass.
-//  4. A butterfly over the row's lanes gives the row totals; the diagonal
-//     block is the lumped mass times I minus the off-diagonal blocks' sum.
+//  4. A butterfly over the row's lanes gives every lane the row totals (FP64:
+//     K and G summed in shared memory instead); the diagonal block is the
+//     lumped mass times I minus the off-diagonal blocks' sum.
 //  5. Every lane writes its own entry (the row's slice of each output array
-//     is contiguous); the diagonal lane writes the right-hand side.
+//     is contiguous); the diagonal block's three compensated diagonal values
+//     and the right-hand side are written by the row's lanes 0-5 (mixed32:
+//     by the diagonal lane).
 // Each element is evaluated once per row of its star (four times per tet).
 // Long rows (more than 32 entries, or a star the row-gather encoder could
 // not cover) are single-row tasks this kernel skips.
@@ -2346,7 +2349,18 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
     __syncwarp();
   }
 
-  // 4. row totals (lanes without an off-diagonal entry hold zeros)
+  // 4. row totals (lanes without an off-diagonal entry hold zeros).  The
+  // merge adds the error terms first (a commutative sum), so both lanes of a
+  // butterfly pair, and in the end every lane of the row, hold bitwise the
+  // same totals.
+  auto merge_sym = [](Acc<P>& a, const Acc<P>& b) {
+    if constexpr (P == NSI_MIXED_F32_ACC64) {
+      a.lo += b.lo;
+      a.add(b.hi);
+    } else {
+      a.v += b.v;
+    }
+  };
   Acc<P> tA, tD;
   tA.zero();
   tD.zero();
@@ -2368,57 +2382,112 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
       xA.v = __shfl_xor_sync(FULL, tA.v, o);
       xD.v = __shfl_xor_sync(FULL, tD.v, o);
     }
-    acc_merge<P>(tA, xA);
-    acc_merge<P>(tD, xD);
+    merge_sym(tA, xA);
+    merge_sym(tD, xD);
+    if constexpr (P != NSI_FP64) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) tK[c] += __shfl_xor_sync(FULL, tK[c], o);
+      for (int c = 0; c < 9; ++c) tK[c] += __shfl_xor_sync(FULL, tK[c], o);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tG[c] += __shfl_xor_sync(FULL, tG[c], o);
+      for (int c = 0; c < 3; ++c) tG[c] += __shfl_xor_sync(FULL, tG[c], o);
+    }
+  }
+  if constexpr (P == NSI_FP64) {
+    // K and G totals in FP64 (a shuffled double is two shuffles): each lane's
+    // values to shared memory (the element records' space, free now), the
+    // row's lanes 0-11 each sum one value over the row's entries in lane
+    // order, then every lane reads the totals
+    T* red = reinterpret_cast<T*>(el);  // [32 lanes][13], then [2 rows][12] totals
+    T* tot = red + 32 * 13;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) red[lane * 13 + c] = K[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) red[lane * 13 + 9 + c] = G[c];
+    __syncwarp();
+    if (q < 12) {
+      T sum = T(0);
+      for (int r = 0; r < len; ++r) sum += red[(seg * width + r) * 13 + q];
+      tot[seg * 12 + q] = sum;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tK[c] = tot[seg * 12 + c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tG[c] = tot[seg * 12 + 9 + c];
   }
 
-  // 5. write-out
+  // 5. write-out: every lane its own entry.  mixed64 and FP64: the row's six
+  // compensated values (the diagonal components of the diagonal block and
+  // the right-hand side) by the row's lanes 0-5, one each, from the totals
+  // every lane holds (the diagonal lane alone took them in turn: 2% of the
+  // kernel in mixed64); mixed32, whose values are plain floats, keeps them on
+  // the diagonal lane (the spread costs it 2%).
   Out* A = static_cast<Out*>(Auu);
   Out* Go = static_cast<Out*>(Gv);
   Out* Rh = static_cast<Out*>(rhs);
-  if (has) {
-    const int64_t g = (int64_t)rs + q;
-    if (q == dp) {
-      const Acc<P> mass = acc_scale<P>(acc_third<P>(tD), kmass);
-      Acc<P> dA = mass;
-      if constexpr (P == NSI_MIXED_F32_ACC64) {
-        dA.add(-tA.hi);
-        dA.lo -= tA.lo;
+  if constexpr (P == NSI_MIXED_F32_ACC32) {
+    if (has) {
+      const int64_t g = (int64_t)rs + q;
+      if (q == dp) {
+        const Acc<P> mass = acc_scale<P>(acc_third<P>(tD), kmass);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) A[c * m.nnz + g] = c % 4 == 0 ? mass.v - tA.v - tK[c] : -tK[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = tG[c] * (kg / T(3));
+        const V3<T> un = load_vec<T>(f.un, i);
+        Rh[i] = mass.v * un.x;
+        Rh[m.n + i] = mass.v * un.y;
+        Rh[2 * m.n + i] = mass.v * un.z;
       } else {
-        dA.v = mass.v - tA.v;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) A[c * m.nnz + g] = c % 4 == 0 ? sA + K[c] : K[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = G[c] * kg;
       }
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        if (c % 4 == 0) {
-          Acc<P> x = dA;
-          x.add(-tK[c]);
-          store_acc(A + c * m.nnz + g, x);
-        } else {
-          A[c * m.nnz + g] = (Out)(-tK[c]);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(tG[c] * (kg / T(3)));
-      const V3<T> un = load_vec<T>(f.un, i);
-      store_acc(Rh + i, acc_scale<P>(mass, un.x));
-      store_acc(Rh + m.n + i, acc_scale<P>(mass, un.y));
-      store_acc(Rh + 2 * m.n + i, acc_scale<P>(mass, un.z));
-    } else {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        A[c * m.nnz + g] = (Out)(c % 4 == 0 ? sA + K[c] : K[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(G[c] * kg);
+    } else if (q == 0 && len == 0) {  // a node in no element: zero right-hand side
+      Rh[i] = 0.0f;
+      Rh[m.n + i] = 0.0f;
+      Rh[2 * m.n + i] = 0.0f;
     }
-  } else if (q == 0 && len == 0) {  // a node in no element: zero right-hand side
-    Rh[i] = Out(0);
-    Rh[m.n + i] = Out(0);
-    Rh[2 * m.n + i] = Out(0);
+  } else {
+    if (has) {
+      const int64_t g = (int64_t)rs + q;
+      if (q == dp) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c)
+          if (c % 4 != 0) A[c * m.nnz + g] = (Out)(-tK[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(tG[c] * (kg / T(3)));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          A[c * m.nnz + g] = (Out)(c % 4 == 0 ? sA + K[c] : K[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Go[c * m.nnz + g] = (Out)(G[c] * kg);
+      }
+    }
+    if (len > 0 && q < 6) {  // (a row's lanes number 16 or 32)
+      const Acc<P> mass = acc_scale<P>(acc_third<P>(tD), kmass);
+      if (q < 3) {  // A(i,i)[c][c] = lumped mass - sum of the row's off-diagonal A - sum of K[c][c]
+        Acc<P> x = mass;
+        if constexpr (P == NSI_MIXED_F32_ACC64) {
+          x.add(-tA.hi);
+          x.lo -= tA.lo;
+        } else {
+          x.v = mass.v - tA.v;
+        }
+        x.add(-(q == 0 ? tK[0] : q == 1 ? tK[4] : tK[8]));
+        store_acc(A + 4 * q * m.nnz + rs + dp, x);
+      } else {  // rhs[k][i] = lumped mass * u^n_k
+        const int k = q - 3;
+        const T* un = static_cast<const T*>(k == 0 ? f.un[0] : k == 1 ? f.un[1] : f.un[2]);
+        store_acc(Rh + k * m.n + i, acc_scale<P>(mass, __ldg(un + i)));
+      }
+    } else if (q == 0 && len == 0) {  // a node in no element: zero right-hand side
+      Rh[i] = Out(0);
+      Rh[m.n + i] = Out(0);
+      Rh[2 * m.n + i] = Out(0);
+    }
   }
 }
 
