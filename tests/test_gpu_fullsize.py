@@ -90,7 +90,7 @@ def cube100_oracle(cube100):
     return full
 
 
-@pytest.mark.parametrize("precision", ["mixed64", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed64", "mixed32", "fp64"])
 def test_cube100_every_row(cube100, cube100_oracle, precision):
     """Every row of A, G and rhs at the headline size (6 M tets), in the launch
     configuration bench.py times, element by element against the oracle:
