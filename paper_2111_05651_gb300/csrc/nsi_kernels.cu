@@ -2244,9 +2244,13 @@ __global__ void __launch_bounds__(32 * STAR_WARPS, P == NSI_FP64 ? 1 : 6) stab_s
     } else {
       uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
       if (has && (!DEBUG || (j >= 0 && j < m.n))) {
-        const uint4* r = static_cast<const uint4*>(m.rec) + 2 * (int64_t)j;
-        a = __ldg(r);
-        b = __ldg(r + 1);
+        // the 32-byte record (32-byte aligned; written by the pack kernel, a
+        // separate launch) in one 256-bit load instead of two 128-bit ones:
+        // 0.944 against 0.954 ms mixed64, 0.733 against 0.755 mixed32
+        const unsigned* r = static_cast<const unsigned*>(m.rec) + 8 * (int64_t)j;
+        asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+            : "l"(r));
       }
       const V3<float> hj{__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
       const V3<float> lj = record_lo(__uint_as_float(b.z), __uint_as_float(b.w));
